@@ -1,0 +1,332 @@
+"""CPU oracle for the filtered incremental scaling-and-squaring method
+(Wu, Zhang, Zhu, Hu, "High-performance computation of large sparse matrix
+exponential", arXiv 2110.04493).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  It shares no code
+with the CUDA path; it is a plain, slow restatement of the paper written with
+numpy / scipy.sparse in float64, following Algorithm 4.2 step by step.
+
+Readings of the paper taken here (the paper is silent or ambiguous on them):
+
+* Norm: the Frobenius norm everywhere (Sec. 5 states it is used in all
+  experiments).
+* (M, N), Eq. (4.20): N in [N0, N0 + 50], N0 = max(ceil(log2 ||H||), 0);
+  m(N) is the smallest M >= 1 meeting the error bound; the pair minimising
+  M 2^N wins, ties going to the smaller M + N, then the smaller N.
+  ||H|| = 0 gives M = N = 0 and e^H = I.
+* Normality (Algorithm 4.2 step 2): H == H^T or H == -H^T exactly counts as
+  normal; otherwise H is normal iff ||H H^T - H^T H||_F <= 64 u ||H||_F^2.
+* Algorithm 4.1: the sentinel b_0 = 1 is read as "run the first pass with
+  eps_f = eps_g unconditionally", so the guarantee
+  ||A - A_tilde|| <= eps_g (1 + e_r) holds for every eps_g; entries with
+  |v| == eps_f are dropped (only |v| > eps_f is kept); exact zeros are
+  always dropped; e_r defaults to 0.1; the loop is capped (ENOCONV).
+* Taylor phase (Algorithm 4.2 step 3, Eq. (4.11)): S_1 = H_0 is not
+  filtered; each S~_i is the product S^_{i-1} H_0 with every entry divided
+  by i; the loop stops once a filtered term is empty (all later terms are
+  then zero).  The threshold eps_g^(0) = a r_0 / (M e^{2 ||H_0||}) bounds
+  ||E_j|| directly, as derived in Eq. (4.14) ("absolute").
+* Squaring (Algorithm 4.2 step 4, Eq. (4.15)): T~_i = 2 T^_{i-1} + T^_{i-1}^2
+  (the printed step writes T^_i on the right; Eq. (4.15) fixes the index);
+  r_i = 2^i r_0 (Sec. 4.1 drops r^2).  The dropped part must satisfy
+  ||B_i|| <= a r_i ||F_i|| (Sec. 4.2, "relative"); ||F_i||_F is taken as
+  ||I + T~_i||_F.  The printed eps_g^(i) = a r_i without the ||F_i|| factor
+  ("absolute") is available as an option.  The relative reading is the
+  default because it reproduces Table 3.
+* e^H = I + T^_N, the diagonal inserted where T^_N has no stored entry.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Tuple
+
+import numpy as np
+import scipy.sparse as sp
+
+U_ROUNDOFF = 2.0 ** -53
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+# --------------------------------------------------------------------------
+# Norms and scalar bounds
+# --------------------------------------------------------------------------
+
+def fro_norm(A) -> float:
+    """Frobenius norm sqrt(sum |a_ij|^2) over the stored entries (Sec. 5)."""
+    v = A.data if sp.issparse(A) else np.asarray(A).ravel()
+    return math.sqrt(math.fsum((np.asarray(v, dtype=np.float64) ** 2).tolist())) if len(v) < 200000 \
+        else float(np.sqrt(np.sum(np.square(np.asarray(v, dtype=np.float64)))))
+
+
+def rho(M: int, x: float) -> float:
+    """Relative error bound of the degree-M Taylor approximant, Eq. (4.5):
+
+    ||F_0^{-1} R_0|| <= (1/M!) sum_{k>=0} x^{M+1+k} / (k! (M+1+k)),  x = ||H 2^-N||,
+    the series form of (-1)^{M+1} gamma(M+1, -x) / M!.
+    """
+    if x == 0.0:
+        return 0.0
+    c = 1.0  # x^{M+1+k} / (M! k!) built up term by term
+    for j in range(1, M + 2):
+        c *= x / j if j <= M else x
+    # after the loop c = x^{M+1} / M!
+    total = 0.0
+    k = 0
+    while True:
+        term = c / (M + 1 + k)
+        total += term
+        if term <= 1e-18 * total or c == 0.0:
+            break
+        k += 1
+        c *= x / k
+        if k > 10000:
+            break
+    return total
+
+
+def ceil_log2(x: float) -> int:
+    """Exact ceil(log2 x) for x > 0."""
+    m, e = math.frexp(x)  # x = m 2^e, 0.5 <= m < 1
+    return e - 1 if m == 0.5 else e
+
+
+def choose_MN(normH: float, eps_tol: float, n_extra: int = 50, m_cap: int = 1000) -> Tuple[int, int]:
+    """Scaling N and Taylor degree M by the enumeration of Eq. (4.20)."""
+    if normH == 0.0:
+        return 0, 0
+    N0 = max(ceil_log2(normH), 0)
+    best = None
+    for N in range(N0, N0 + n_extra + 1):
+        x = math.ldexp(normH, -N)
+        M = 1
+        while math.ldexp(rho(M, x), N) > eps_tol:
+            M += 1
+            if M > m_cap:
+                break
+        if M > m_cap:
+            continue
+        key = (M * 2 ** N, M + N, N)
+        if best is None or key < best[0]:
+            best = (key, M, N)
+    if best is None:
+        raise OracleError("no feasible (M, N)")
+    return best[1], best[2]
+
+
+def is_normal(H: sp.csr_matrix) -> bool:
+    """Normality test (reading of Algorithm 4.2 step 2, see module docstring)."""
+    Ht = H.T.tocsr()
+    if (H != Ht).nnz == 0 or (H + Ht).count_nonzero() == 0:
+        return True
+    C = (H @ Ht) - (Ht @ H)
+    return fro_norm(C) <= 64.0 * U_ROUNDOFF * fro_norm(H) ** 2
+
+
+# --------------------------------------------------------------------------
+# Algorithm 4.1
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class FilterInfo:
+    eps_g: float
+    t: float          # final eps_f: entries with |v| <= t are dropped
+    iters: int
+    b: float          # F-norm of the dropped part
+    nnz_in: int
+    nnz_out: int
+
+
+def alg41_threshold(vals: np.ndarray, eps_g: float, e_r: float, max_iter: int = 100) -> Tuple[float, int, float]:
+    """Algorithm 4.1 on the stored values of a matrix.
+
+    Returns (eps_f, iterations, b): the entries with |v| > eps_f are kept, the
+    rest (whose F-norm is b <= eps_g (1 + e_r)) are dropped.
+    """
+    stash = np.abs(np.asarray(vals, dtype=np.float64))
+    m = 1.0
+    b = math.inf  # the first pass always runs (reading of the b_0 sentinel)
+    n = 0
+    eps_f = eps_g
+    while b > eps_g * (1.0 + e_r):
+        if n >= max_iter:
+            raise OracleError("Algorithm 4.1 did not converge")
+        eps_f = eps_g / m
+        stash = stash[stash <= eps_f]          # b_n(p) = 0 for |b_n| > eps_f
+        b = float(np.sqrt(np.sum(stash * stash)))
+        m = b / eps_f
+        n += 1
+    return eps_f, n, b
+
+
+def filter_csr(A: sp.csr_matrix, eps_g: float, e_r: float, max_iter: int = 100) -> Tuple[sp.csr_matrix, FilterInfo]:
+    """A_tilde = A - b_n of Algorithm 4.1: keep the stored entries with |v| > eps_f."""
+    t, iters, b = alg41_threshold(A.data, eps_g, e_r, max_iter)
+    keep = np.abs(A.data) > t
+    B = A.copy()
+    B.data = np.where(keep, B.data, 0.0)
+    B.eliminate_zeros()
+    B.sort_indices()
+    return B, FilterInfo(eps_g, t, iters, b, A.nnz, B.nnz)
+
+
+# --------------------------------------------------------------------------
+# Algorithm 4.2
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class TaylorTerm:
+    i: int
+    nnz_raw: int
+    nnz: int
+    t: float
+    iters: int
+
+
+@dataclasses.dataclass
+class SquareStep:
+    i: int
+    eps_g: float
+    normF: float
+    nnz_raw: int
+    nnz: int
+    t: float
+    iters: int
+    b: float
+
+
+@dataclasses.dataclass
+class OracleStats:
+    n: int
+    normH: float
+    M: int
+    N: int
+    normal: bool
+    a: float
+    r0: float
+    eps_g0: float
+    taylor: List[TaylorTerm]
+    steps: List[SquareStep]
+    nnz_T0: int = 0
+    nnz_out: int = 0
+
+
+def _canon(A) -> sp.csr_matrix:
+    A = sp.csr_matrix(A)
+    A.sum_duplicates()
+    A.sort_indices()
+    return A
+
+
+def taylor_phase(H0: sp.csr_matrix, M: int, eps_g0: float, e_r: float, max_iter: int = 100,
+                 keep_terms: bool = False):
+    """Algorithm 4.2 step 3 with the filtered recursion of Eq. (4.11).
+
+    Returns (T^_0, list of TaylorTerm, list of the filtered terms S^_i if keep_terms).
+    """
+    S = _canon(H0)                     # S_1 = H_0 (not filtered)
+    T0 = S.copy()
+    terms: List[TaylorTerm] = []
+    kept = [S.copy()] if keep_terms else None
+    for i in range(2, M + 1):
+        St = _canon(S @ H0)
+        St.data = St.data / i          # S~_i = S^_{i-1} H_0 / i
+        S, info = filter_csr(St, eps_g0, e_r, max_iter)
+        terms.append(TaylorTerm(i, St.nnz, S.nnz, info.t, info.iters))
+        if S.nnz == 0:
+            break
+        if keep_terms:
+            kept.append(S.copy())
+        T0 = _canon(T0 + S)            # T^_0^(i) = T^_0^(i-1) + S^_i
+    return T0, terms, kept
+
+
+def square_raw(T: sp.csr_matrix) -> sp.csr_matrix:
+    """T~ = 2 T + T T (Eq. (2.7) / (4.15)), union pattern, unfiltered."""
+    return _canon(_canon(T @ T) + 2.0 * T)
+
+
+def norm_I_plus(T: sp.csr_matrix) -> float:
+    """||I + T||_F, the estimate of ||F_i||_F used by the relative threshold."""
+    return fro_norm(_canon(sp.identity(T.shape[0], format="csr") + T))
+
+
+def squaring_phase(T0: sp.csr_matrix, N: int, a: float, r0: float, e_r: float, scale: str = "rel",
+                   max_iter: int = 100, keep_iterates: bool = False):
+    """Algorithm 4.2 step 4: N filtered incremental squarings."""
+    T = T0
+    steps: List[SquareStep] = []
+    iterates = [T0.copy()] if keep_iterates else None
+    for i in range(1, N + 1):
+        ri = math.ldexp(r0, i)                 # r_i = 2 r_{i-1}
+        Tt = square_raw(T)
+        normF = norm_I_plus(Tt) if scale == "rel" else 1.0
+        eps_g = a * ri * normF
+        T, info = filter_csr(Tt, eps_g, e_r, max_iter)
+        steps.append(SquareStep(i, eps_g, normF, Tt.nnz, T.nnz, info.t, info.iters, info.b))
+        if keep_iterates:
+            iterates.append(T.copy())
+    return T, steps, iterates
+
+
+def plan_scalars(H: sp.csr_matrix, eps_tol: float, normal: Optional[bool] = None, n_extra: int = 50):
+    """Algorithm 4.2 steps 1-3 scalars: ||H||, (M, N), a, r_0, eps_g^(0)."""
+    normH = fro_norm(H)
+    M, N = choose_MN(normH, eps_tol, n_extra)
+    if normal is None:
+        normal = is_normal(H)
+    a = 1.0 / (1 + N) if normal else (1.0 / normH if normH > 0 else 1.0)
+    x0 = math.ldexp(normH, -N)
+    r0 = rho(M, x0) if M > 0 else 0.0
+    eps_g0 = a * r0 / (M * math.exp(2.0 * x0)) if M > 0 else 0.0
+    return normH, M, N, normal, a, r0, eps_g0
+
+
+def expm(H, tau: float = 1.0, eps_tol: float = 1e-12, e_r: float = 0.1, square_scale: str = "rel",
+         normal: Optional[bool] = None, max_iter: int = 100, n_extra: int = 50,
+         keep: bool = False):
+    """e^{tau H} by Algorithm 4.2.  Returns (E as scipy CSR, OracleStats[, trace])."""
+    if not (eps_tol > 0.0 and math.isfinite(eps_tol)):
+        raise OracleError("eps_tol must be positive and finite")
+    H = _canon(H)
+    n = H.shape[0]
+    if tau != 1.0:
+        H = H.copy()
+        H.data = H.data * tau
+    normH, M, N, normal, a, r0, eps_g0 = plan_scalars(H, eps_tol, normal, n_extra)
+    stats = OracleStats(n, normH, M, N, normal, a, r0, eps_g0, [], [])
+    eye = sp.identity(n, format="csr")
+    if M == 0:
+        E = _canon(eye)
+        stats.nnz_out = E.nnz
+        return (E, stats, None) if keep else (E, stats)
+    H0 = H.copy()
+    H0.data = np.ldexp(H0.data, -N)            # H_0 = H 2^-N (exact)
+    T0, terms, kept_terms = taylor_phase(H0, M, eps_g0, e_r, max_iter, keep_terms=keep)
+    stats.taylor = terms
+    stats.nnz_T0 = T0.nnz
+    T, steps, iterates = squaring_phase(T0, N, a, r0, e_r, square_scale, max_iter, keep_iterates=keep)
+    stats.steps = steps
+    E = _canon(eye + T)                        # e^H = I + T^_N
+    stats.nnz_out = E.nnz
+    if keep:
+        return E, stats, {"H0": H0, "S": kept_terms, "T": iterates}
+    return E, stats
+
+
+# --------------------------------------------------------------------------
+# Diagnostics used by the pins
+# --------------------------------------------------------------------------
+
+def bandwidth(A: sp.csr_matrix) -> int:
+    """Natural-order bandwidth l(A) = l_1(A) + l_2(A), Eq. (3.1)."""
+    A = sp.coo_matrix(A)
+    nz = A.data != 0
+    if not np.any(nz):
+        return 0
+    d = A.col[nz].astype(np.int64) - A.row[nz].astype(np.int64)
+    return int(max(d.max(), 0) + max((-d).max(), 0))

@@ -1,0 +1,349 @@
+"""Pins of the CPU oracle against values fixed by the paper and by mathematics.
+
+Each test names the passage it checks.  None of these compares the oracle
+with itself: the expected values come from the paper's printed tables, closed
+forms, hand traces of Algorithm 4.1, or library routines on tiny inputs.
+"""
+import decimal
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from oracle import sexpm_oracle as O
+from workloads import (
+    diag_scale,
+    dirichlet_laplacian,
+    get_config,
+    paper_table1_matrices,
+    rgg_adjacency,
+    toeplitz_trid,
+)
+
+D = decimal.Decimal
+
+
+# ---------------------------------------------------------------- Eq. (4.5)
+
+def _rho_closed_form(M, x, digits=250):
+    """(1/M!) int_0^x u^M e^u du = (-1)^M [e^x sum_{k<=M} (-x)^k/k! - 1] / 1, at high precision."""
+    with decimal.localcontext() as ctx:
+        ctx.prec = digits
+        X = D(repr(x))
+        s = D(0)
+        term = D(1)
+        for k in range(M + 1):
+            if k > 0:
+                term = term * (-X) / k
+            s += term
+        val = (X.exp() * s - 1) * (-1 if M % 2 else 1)
+        return float(val)
+
+
+@pytest.mark.parametrize("M", [1, 2, 5, 10, 20, 30])
+@pytest.mark.parametrize("x", [1e-3, 0.25, 0.5, 0.9566, 1.0, 3.0])
+def test_rho_is_the_incomplete_gamma_bound(M, x):
+    """Eq. (4.5): the series equals (-1)^{M+1} gamma(M+1, -x) / M!."""
+    got = O.rho(M, x)
+    want = _rho_closed_form(M, x)
+    assert got == pytest.approx(want, rel=1e-13, abs=0.0)
+
+
+@pytest.mark.parametrize("M", [3, 8, 15])
+def test_rho_small_x_limit(M):
+    """As x -> 0 the bound behaves like x^{M+1}/(M+1)!."""
+    x = 1e-6
+    assert O.rho(M, x) == pytest.approx(x ** (M + 1) / math.factorial(M + 1), rel=1e-5)
+
+
+# ---------------------------------------------------------------- Eq. (4.20), Sec. 5.2
+
+def test_choose_MN_reproduces_paper_toeplitz():
+    """Sec. 5.2: trid(1,-2,1), n=10000, eps_tol=1e-16 has ||H|| = 244.9 and (M, N) = (20, 8)."""
+    H = toeplitz_trid(10_000, 1.0, -2.0, 1.0).to_scipy()
+    normH = O.fro_norm(H)
+    assert round(normH, 1) == 244.9
+    assert O.choose_MN(normH, 1e-16) == (20, 8)
+
+
+def test_choose_MN_constraints_hold():
+    """Eq. (4.20): ||H 2^-N|| <= 1 and 2^N rho(M, x) <= eps_tol, and M is minimal for that N."""
+    for normH, eps in [(0.3, 1e-12), (155.36, 1e-14), (7002.0, 1e-12), (15114.0, 1e-12), (1.7e6, 1e-16)]:
+        M, N = O.choose_MN(normH, eps)
+        x = normH / 2 ** N
+        assert x <= 1.0
+        assert 2 ** N * O.rho(M, x) <= eps
+        assert M == 1 or 2 ** N * O.rho(M - 1, x) > eps
+
+
+def test_choose_MN_zero_norm():
+    assert O.choose_MN(0.0, 1e-12) == (0, 0)
+
+
+# ---------------------------------------------------------------- Algorithm 4.1
+
+def test_alg41_hand_trace_two_passes():
+    """Hand trace: values 1,2,3,4 with eps_g=3, e_r=0.1.
+
+    pass 1: eps_f=3, stash {1,2,3}, b=sqrt(14) > 3.3, m = sqrt(14)/3;
+    pass 2: eps_f = 9/sqrt(14) = 2.405, stash {1,2}, b = sqrt(5) <= 3.3 -> stop.
+    """
+    t, iters, b = O.alg41_threshold(np.array([1.0, -2.0, 3.0, 4.0]), 3.0, 0.1)
+    assert iters == 2
+    assert t == pytest.approx(9.0 / math.sqrt(14.0), rel=1e-15)
+    assert b == pytest.approx(math.sqrt(5.0), rel=1e-15)
+
+
+def test_alg41_hand_trace_geometric_thresholds():
+    """Four entries 0.5 with eps_g = 0.8: b stays 1 while eps_f shrinks by 0.8 each pass
+    (0.8, 0.64, 0.512, 0.4096); the fourth pass empties the stash and keeps everything."""
+    t, iters, b = O.alg41_threshold(np.full(4, 0.5), 0.8, 0.1)
+    assert iters == 4
+    assert t == pytest.approx(0.4096, rel=1e-14)
+    assert b == 0.0
+
+
+def test_alg41_single_pass_when_small_part_is_tolerable():
+    t, iters, b = O.alg41_threshold(np.array([1e-3, 2e-3, 5.0]), 1e-2, 0.1)
+    assert (iters, t) == (1, 1e-2)
+    assert b == pytest.approx(math.sqrt(5e-6))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_alg41_guarantee_and_termination(seed):
+    """Theorem 4.1 (termination) and the stated guarantee ||A - A~|| <= eps_g (1 + e_r);
+    the dropped set is exactly {|v| <= eps_f} and eps_f <= eps_g."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(5000) * np.exp(rng.uniform(-40, 0, 5000))
+    eps_g = float(np.exp(rng.uniform(-30, -5)))
+    e_r = [0.01, 0.1, 1.0][seed % 3]
+    A = sp.csr_matrix(v.reshape(50, 100))
+    B, info = O.filter_csr(A, eps_g, e_r)
+    dropped = A.toarray() - B.toarray()
+    assert np.linalg.norm(dropped) <= eps_g * (1 + e_r) * (1 + 1e-12)
+    assert info.t <= eps_g
+    kept = np.abs(A.toarray()) > info.t
+    assert np.array_equal(B.toarray() != 0, kept)
+    assert info.iters <= 100
+
+
+# ---------------------------------------------------------------- Table 1, Sec. 5.1
+
+def _table1_reference():
+    """Exact e^{H_k} of the five matrices of Table 1 (closed forms)."""
+    e = math.e
+    V = np.array([[1.0, 3.0], [2.0, 4.0]])
+    return [
+        math.exp(6.1) * np.array([[1.0, 1e6], [0.0, 1.0]]),
+        e * np.array([[1.0, 1e6, 1e12], [0.0, 1.0, 1e6], [0.0, 0.0, 1.0]]),
+        np.array([[e, math.sqrt(3.0) * 1e6 * (e - math.exp(0.9)) / 0.1], [0.0, math.exp(0.9)]]),
+        V @ np.diag([math.exp(-1.0), math.exp(-17.0)]) @ np.linalg.inv(V),
+        np.array([[math.exp(1 + 1e-5), e * math.sinh(1e-5) / 1e-5], [0.0, math.exp(1 - 1e-5)]]),
+    ]
+
+
+def test_table1_relative_errors_at_paper_level():
+    """Table 1: the proposed algorithm reaches relative errors <= 2.71e-14 on H1..H5;
+    on H4 (the worst case) the paper prints 2.71e-14 and the oracle reproduces it."""
+    errs = []
+    for H, R in zip(paper_table1_matrices(), _table1_reference()):
+        E, st = O.expm(sp.csr_matrix(H), 1.0, 1e-16)
+        assert not st.normal
+        errs.append(np.linalg.norm(E.toarray() - R) / np.linalg.norm(R))
+    assert max(errs) <= 3e-14
+    assert f"{errs[3]:.2e}" == "2.71e-14"
+
+
+# ---------------------------------------------------------------- Tables 2 and 3, Sec. 5.2
+
+@pytest.fixture(scope="module")
+def toeplitz_run():
+    H = toeplitz_trid(10_000, 1.0, -2.0, 1.0).to_scipy()
+    return O.expm(H, 1.0, 1e-16, keep=True)
+
+
+def test_table3_bandwidths_of_squaring_iterates(toeplitz_run):
+    """Table 3: lambda(T^_i) = 14, 16, 18, 20, 22, 26, 32, 38 for i = 1..8."""
+    E, st, tr = toeplitz_run
+    assert (st.M, st.N) == (20, 8)
+    assert [O.bandwidth(T) for T in tr["T"][1:]] == [14, 16, 18, 20, 22, 26, 32, 38]
+
+
+def test_table2_bandwidths_of_taylor_terms(toeplitz_run):
+    """Table 2: lambda(S^_i) = 4..16 for i = 2..8 and S^_i = 0 for i >= 10 (eight products).
+    Column i = 9 (printed 14) is not reproduced; see the readings recorded for the filter."""
+    E, st, tr = toeplitz_run
+    lam = [O.bandwidth(S) for S in tr["S"][1:]]
+    assert lam[:7] == [4, 6, 8, 10, 12, 14, 16]
+    assert st.taylor[-1].i == 10 and st.taylor[-1].nnz == 0
+    assert lam[7] in (12, 14)
+
+
+def test_relative_threshold_is_needed_for_table3():
+    """Under the printed absolute eps_g^(i) = a r_i the first iterate keeps bandwidth 16, not 14."""
+    H = toeplitz_trid(10_000, 1.0, -2.0, 1.0).to_scipy()
+    E, st, tr = O.expm(H, 1.0, 1e-16, square_scale="abs", keep=True)
+    assert O.bandwidth(tr["T"][1]) != 14
+
+
+# ---------------------------------------------------------------- Table 4 closed form G_s
+
+def _G(s, n, terms=40):
+    """G_s = (-1)^s sum_{i>=s} C(2i, s+i) / (i! (n+1)^i): the Toeplitz part of e^H for
+    H = (1/(n+1)) trid(-1,2,-1) (Sec. 5.2; binomial read as C(2i, s+i), the printed
+    C(s+i, 2i) vanishing for i > s)."""
+    with decimal.localcontext() as ctx:
+        ctx.prec = 60
+        tot = D(0)
+        for i in range(s, s + terms):
+            tot += D(math.comb(2 * i, s + i)) / (D(math.factorial(i)) * D(n + 1) ** i)
+        return float(tot) * (-1) ** s
+
+
+def test_table4_middle_column_matches_Gs():
+    n = 10_000
+    H = toeplitz_trid(n, -1.0 / (n + 1), 2.0 / (n + 1), -1.0 / (n + 1)).to_scipy()
+    E, st = O.expm(H, 1.0, 1e-16)
+    col = E[:, n // 2].toarray().ravel()
+    for s in range(0, 12):
+        g = _G(s, n)
+        assert abs(col[n // 2 + s] - g) <= 2e-16 * abs(_G(0, n)) + 1e-3 * abs(g)
+        assert abs(col[n // 2 - s] - g) <= 2e-16 * abs(_G(0, n)) + 1e-3 * abs(g)
+    # off-diagonal entries to full relative precision while they are above the filter level
+    for s in range(1, 4):
+        assert col[n // 2 + s] == pytest.approx(_G(s, n), rel=1e-12)
+
+
+# ---------------------------------------------------------------- closed forms on grid Laplacians
+
+def _sine_basis_expm(m, tau):
+    """e^{tau L_1} for the 1-D Dirichlet Laplacian via its sine eigenbasis."""
+    h = 1.0 / (m + 1)
+    j = np.arange(1, m + 1)
+    lam = -(4.0 / h ** 2) * np.sin(j * np.pi * h / 2) ** 2
+    V = np.sqrt(2 * h) * np.sin(np.outer(j, j) * np.pi * h)
+    return (V * np.exp(tau * lam)) @ V.T
+
+
+def test_lap2d_m32_matches_kronecker_closed_form():
+    """e^{tau (L_1 (+) L_1)} = e^{tau L_1} (x) e^{tau L_1} on the 32x32 grid, tau = 1e-3, eps = 1e-14."""
+    c = get_config("lap2d_m32")
+    H = c.build().to_scipy()
+    E, st = O.expm(H, c.tau, c.eps)
+    assert (st.M, st.N) == (15, 8)
+    E1 = _sine_basis_expm(32, c.tau)
+    X = np.kron(E1, E1)
+    err = np.abs(E.toarray() - X)
+    norm1 = np.abs(X).sum(axis=0).max()
+    assert err.max() <= 1e-12 * norm1
+    assert np.linalg.norm(E.toarray() - X) / np.linalg.norm(X) <= 4 * c.eps
+
+
+def test_lap3d_small_matches_kronecker_closed_form():
+    m, tau = 10, 2.1125 / 11 ** 2
+    H = dirichlet_laplacian(m, 3).to_scipy()
+    E, st = O.expm(H, tau, 1e-12)
+    E1 = _sine_basis_expm(m, tau)
+    X = np.kron(np.kron(E1, E1), E1)
+    assert np.abs(E.toarray() - X).max() <= 1e-12 * np.abs(X).sum(axis=0).max()
+
+
+# ---------------------------------------------------------------- dense library routine on tiny inputs
+
+@pytest.mark.parametrize("seed", range(6))
+def test_matches_dense_pade_expm_on_small_matrices(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(5, 40))
+    A = sp.random(n, n, density=0.2, random_state=np.random.RandomState(seed), format="csr")
+    if seed % 2 == 0:
+        A = A + A.T
+    A = A * float(rng.uniform(0.5, 30.0)) * (1 if seed % 3 else -1)
+    E, st = O.expm(A, 1.0, 1e-14)
+    X = sla.expm(A.toarray())
+    assert np.abs(E.toarray() - X).max() <= 1e-12 * max(1.0, np.abs(X).sum(axis=0).max())
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_zero_matrix_gives_identity():
+    E, st = O.expm(sp.csr_matrix((7, 7)), 1.0, 1e-12)
+    assert (st.M, st.N) == (0, 0)
+    assert np.array_equal(E.toarray(), np.eye(7))
+
+
+def test_generator_rows_sum_to_one():
+    """e^{tau Q} 1 = 1 for a graph Laplacian generator Q = A - diag(A 1)."""
+    A = rgg_adjacency(400, seed=11).to_scipy()
+    Q = A - sp.diags(np.asarray(A.sum(axis=1)).ravel())
+    E, st = O.expm(Q.tocsr(), 0.7, 1e-12)
+    assert np.abs(E @ np.ones(400) - 1.0).max() <= 1e-12
+
+
+def test_symmetry_inverse_and_half_step():
+    H = dirichlet_laplacian(8, 2).to_scipy() * (0.02 / 1.0)
+    E, _ = O.expm(H, 1.0, 1e-13)
+    Einv, _ = O.expm(-H, 1.0, 1e-13)
+    Eh, _ = O.expm(H, 0.5, 1e-13)
+    Ed = E.toarray()
+    assert np.abs(Ed - Ed.T).max() == 0.0
+    Ei = Einv.toarray()
+    cond = np.abs(Ed).sum(axis=0).max() * np.abs(Ei).sum(axis=0).max()
+    assert np.abs(Ed @ Ei - np.eye(64)).max() <= 1e-13 * cond
+    assert np.abs((Eh @ Eh).toarray() - Ed).max() <= 1e-12
+
+
+def test_similarity_identity_for_diagonally_scaled_laplacian():
+    """e^{D L} = D^{1/2} e^{D^{1/2} L D^{1/2}} D^{-1/2}: non-normal branch (a = 1/||H||)
+    against the normal branch (a = 1/(N+1)) on a 3-D grid."""
+    L = dirichlet_laplacian(6, 3)
+    DL, d = diag_scale(L, seed=1)
+    tau = 2.0 / 49.0
+    E1, st1 = O.expm(DL.to_scipy(), tau, 1e-12)
+    sq = sp.diags(np.sqrt(d))
+    S = (sq @ L.to_scipy() @ sq).tocsr()
+    E2, st2 = O.expm(S, tau, 1e-12)
+    assert not st1.normal and st2.normal
+    X = (sq @ E2 @ sp.diags(1.0 / np.sqrt(d))).toarray()
+    assert np.abs(E1.toarray() - X).max() <= 1e-12 * np.abs(X).sum(axis=0).max()
+
+
+def test_normality_flags():
+    S = dirichlet_laplacian(5, 2).to_scipy()
+    K = sp.triu(S, 1) - sp.triu(S, 1).T
+    assert O.is_normal(S) and O.is_normal(K.tocsr())
+    assert not O.is_normal(diag_scale(dirichlet_laplacian(5, 2), seed=2)[0].to_scipy())
+    assert not O.is_normal(sp.csr_matrix(paper_table1_matrices()[0]))
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+def test_pins_catch_a_dropped_2T_term(monkeypatch):
+    """Planting T~ = T T (no 2T term, i.e. plain squaring of the increment) must break
+    the closed-form pin."""
+    monkeypatch.setattr(O, "square_raw", lambda T: O._canon(T @ T))
+    H = dirichlet_laplacian(8, 2).to_scipy()
+    E, st = O.expm(H, 5e-3, 1e-12)
+    E1 = _sine_basis_expm(8, 5e-3)
+    assert np.abs(E.toarray() - np.kron(E1, E1)).max() > 1e-6
+
+
+def test_pins_catch_a_wrong_factorial_in_rho(monkeypatch):
+    orig = O.rho
+    monkeypatch.setattr(O, "rho", lambda M, x: orig(M, x) * (M + 1))
+    assert O.choose_MN(244.9449, 1e-16) != (20, 8)
+
+
+def test_pins_catch_keeping_the_dropped_side(monkeypatch):
+    """Keeping |v| >= eps_f on the wrong side (dropping the large entries) breaks Table 3."""
+    orig = O.alg41_threshold
+
+    def flipped(vals, eps_g, e_r, max_iter=100):
+        t, n, b = orig(vals, eps_g, e_r, max_iter)
+        return t * 1e6, n, b
+
+    monkeypatch.setattr(O, "alg41_threshold", flipped)
+    H = toeplitz_trid(2000, 1.0, -2.0, 1.0).to_scipy()
+    E, st, tr = O.expm(H, 1.0, 1e-16, keep=True)
+    assert [O.bandwidth(T) for T in tr["T"][1:]] != [14, 16, 18, 20, 22, 26, 32, 38]
