@@ -1,0 +1,192 @@
+/*
+ * sexpm.h - C ABI of the GB300 library for the filtered incremental
+ * scaling-and-squaring method for a large sparse matrix exponential
+ * (Wu, Zhang, Zhu, Hu, arXiv 2110.04493).
+ *
+ * Problem statement (Algorithm 4.2): given a sparse real H (n x n) and an
+ * error tolerance eps_tol, return an approximation of e^{tau H} as a sparse
+ * matrix together with the choices the method made: the scaling N and the
+ * Taylor degree M (Eq. 4.20), the filter parameter a, the error bound r_0
+ * (Eq. 4.5) and the filter thresholds of every Taylor term and squaring step
+ * (Algorithm 4.1).
+ *
+ * Conventions shared by every call:
+ *   - Matrices are square CSR: int64 row pointers (n+1 entries, row_ptr[0]=0,
+ *     non-decreasing), int32 column indices sorted strictly increasing within
+ *     each row, float64 values.  All arithmetic is IEEE float64 on the GPU.
+ *   - Input views are borrowed: the library copies what it needs before the
+ *     call returns and never frees caller memory.
+ *   - Result handles (sexpm_result_t) own device memory allocated by the
+ *     library from its own stream-ordered pool; release them with
+ *     sexpm_result_free().
+ *   - Every call returns an int status (SEXPM_OK = 0 or a negative code);
+ *     no C++ exception crosses this boundary.  sexpm_last_error() returns a
+ *     thread-local message describing the last failure on the calling thread.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).  Calls synchronise that stream before they
+ *     return, because the method reads scalar reductions back to the host
+ *     between kernels (Algorithm 4.1 is a host-driven iteration).
+ */
+#ifndef SEXPM_H_
+#define SEXPM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define SEXPM_OK 0
+#define SEXPM_EINVAL (-1)    /* bad CSR, n mismatch, NaN/Inf, eps <= 0, non-finite tau */
+#define SEXPM_ENOMEM (-2)    /* device or host allocation failed */
+#define SEXPM_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define SEXPM_ENOCONV (-4)   /* Algorithm 4.1 hit its iteration cap */
+#define SEXPM_ENOPARAM (-5)  /* no feasible (M, N) in [N0, N0 + n_extra] */
+#define SEXPM_ETIMEOUT (-6)  /* a bounded device wait gave up */
+#define SEXPM_EOVERFLOW (-7) /* a size exceeded an index type or a fixed capacity */
+
+/* ------------------------------------------------------------------ types */
+
+/* Borrowed square CSR matrix.  on_device = 1: the three arrays are device
+ * pointers of the current device; 0: host pointers. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+  int32_t on_device;
+} sexpm_csr_view;
+
+/* Options.  Fill with sexpm_options_default() and override fields. */
+typedef struct {
+  double e_r;               /* Algorithm 4.1 tolerance e_r (> 0); default 0.1 */
+  int32_t square_scale;     /* 1: ||B_i|| <= a r_i ||I + T~_i||_F (Sec. 4.2, default);
+                               0: ||B_i|| <= a r_i (the value printed in Algorithm 4.2) */
+  int32_t normal_override;  /* -1: test normality; 0: treat H as non-normal; 1: as normal */
+  int32_t max_filter_iters; /* Algorithm 4.1 iteration cap; default 100 */
+  int32_t n_extra;          /* N_max = N_0 + n_extra in Eq. (4.20); default 50 */
+  int32_t max_taylor;       /* cap on M (SEXPM_ENOPARAM above it); default 1000 */
+} sexpm_options;
+
+typedef struct sexpm_plan sexpm_plan_t;
+typedef struct sexpm_result sexpm_result_t;
+
+/* Per Taylor term (i = 2..M') or squaring step (i = 1..N) record. */
+typedef struct {
+  int32_t phase;      /* 0 = Taylor term S^_i, 1 = squaring step T^_i */
+  int32_t i;
+  int32_t iters;      /* Algorithm 4.1 passes */
+  int32_t pad_;
+  double eps_g;       /* bound on the F-norm of the dropped part */
+  double t;           /* final eps_f: stored entries with |v| <= t were dropped */
+  double b;           /* F-norm of the dropped part */
+  double norm_F;      /* ||I + T~_i||_F (squaring steps; 0 for Taylor terms) */
+  int64_t nnz_raw;    /* stored entries before filtering */
+  int64_t nnz;        /* stored entries after filtering */
+  int64_t products;   /* scalar multiply-adds of the sparse product */
+  double ms;          /* device time of the step (CUDA events) */
+  double ms_symbolic; /* sparse product: row analysis, binning and symbolic pass */
+  double ms_numeric;  /* sparse product: numeric pass (fused /i or + 2T) */
+  double ms_filter;   /* Algorithm 4.1 passes, row-pointer scan and compaction */
+  double flops;       /* FP64 operations of the numeric pass: 2 products + the fused term */
+  double bytes_filter;/* algorithmic bytes moved by the filter passes, scan and compaction */
+} sexpm_step_stats;
+
+typedef struct {
+  int64_t n;
+  double norm_H;      /* ||tau H||_F */
+  int32_t M, N;       /* Eq. (4.20) */
+  int32_t normal;     /* 1 if H was treated as normal */
+  int32_t n_steps;    /* entries filled in steps[] (<= max) */
+  double a;           /* filter parameter: 1/(N+1) (normal) or 1/||H||_F */
+  double r0;          /* Eq. (4.5) at x = ||H 2^-N||_F */
+  double eps_g0;      /* a r_0 / (M e^{2 ||H_0||_F}), the Taylor-phase bound */
+  int64_t nnz_out;    /* stored entries of e^{tau H} */
+  double ms_total;    /* device time of sexpm_compute */
+  double ms_taylor;
+  double ms_squaring;
+  double ms_final;
+  int64_t peak_bytes; /* peak device bytes held by the library during compute */
+  int64_t launches;   /* kernels enqueued by the library during compute */
+} sexpm_stats_t;
+
+/* ------------------------------------------------------------------ calls */
+
+/* Fill *opt with the defaults listed above.  Never fails for non-NULL opt. */
+int sexpm_options_default(sexpm_options* opt);
+
+/* Algorithm 4.2 step 1 input: validate H (square, sorted unique columns,
+ * finite values), copy it to the device, compute ||H||_F and the normality
+ * flag (H == H^T or H == -H^T exactly, else ||H H^T - H^T H||_F <= 64 u ||H||_F^2)
+ * on the GPU.  eps is eps_tol of Algorithm 4.2 (> 0, finite).  n must equal
+ * H->n.  opt may be NULL (defaults).  On success *out owns device memory. */
+int sexpm_plan(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_options* opt,
+               void* stream, sexpm_plan_t** out);
+
+/* Algorithm 4.2 for tau*H: (M, N) by Eq. (4.20); a by step 2; the filtered
+ * Taylor phase of Eqs. (4.10)-(4.11); N filtered squarings
+ * T~_i = 2 T^_{i-1} + T^_{i-1}^2 (Eq. 4.15) each filtered by Algorithm 4.1;
+ * e^{tau H} = I + T^_N.  tau must be finite.  *out receives a new result. */
+int sexpm_compute(sexpm_plan_t* plan, double tau, sexpm_result_t** out);
+
+/* Dimension and stored-entry count of a result. */
+int sexpm_result_info(const sexpm_result_t* res, int64_t* n, int64_t* nnz);
+
+/* Copy a result into caller buffers of n+1 / nnz / nnz elements; on_device
+ * selects device (1) or host (0) destination pointers. */
+int sexpm_result_copy(const sexpm_result_t* res, int64_t* row_ptr, int32_t* col, double* val,
+                      int32_t on_device);
+
+/* Scalars and per-step records of the compute that produced res.  steps may
+ * be NULL; otherwise up to max_steps records are written. */
+int sexpm_stats(const sexpm_result_t* res, sexpm_stats_t* stats, sexpm_step_stats* steps,
+                int32_t max_steps);
+
+void sexpm_result_free(sexpm_result_t* res);
+void sexpm_plan_destroy(sexpm_plan_t* plan);
+
+/* Thread-local description of the last failure ("" if none). */
+const char* sexpm_last_error(void);
+
+/* Number of kernels the library has enqueued since it was loaded (all threads). */
+int64_t sexpm_kernel_launches(void);
+
+/* Return the device memory cached by the library's pool on the current device to
+ * the driver (the pool keeps freed blocks for reuse otherwise). */
+int sexpm_release_memory(void);
+
+/* Host-only helpers (no GPU needed): the scalar choices of Algorithm 4.2. */
+
+/* Eq. (4.5): (1/M!) sum_k x^{M+1+k} / (k! (M+1+k)). */
+double sexpm_rho(int32_t M, double x);
+
+/* Eq. (4.20): minimise M 2^N over N in [N0, N0 + n_extra], N0 = max(ceil(log2 norm_H), 0),
+ * M the least positive integer with 2^N rho(M, norm_H 2^-N) <= eps; ties to the smaller
+ * M + N, then the smaller N.  norm_H = 0 gives M = N = 0. */
+int sexpm_choose_MN(double norm_H, double eps, int32_t n_extra, int32_t max_M, int32_t* M, int32_t* N);
+
+/* ------------------------------------------------------------ step calls */
+/* The individual steps of the hot path on caller-provided device CSR views,
+ * for testing and measurement.  Outputs are new result handles. */
+
+/* One sparse product with the fused scaling and sum of Algorithm 4.2:
+ *   C = (A B) / div + beta * D     (D may be NULL; its pattern joins C's).
+ * div = i gives the Taylor term S~_i = S^_{i-1} H_0 / i (Eq. 4.10);
+ * div = 1, beta = 2, D = A = B = T gives T~ = 2T + T T (Eq. 4.15).
+ * Every structurally present entry is stored (exact zeros included).
+ * *products receives the number of scalar multiply-adds. */
+int sexpm_spgemm(const sexpm_csr_view* A, const sexpm_csr_view* B, const sexpm_csr_view* D,
+                 double div, double beta, void* stream, sexpm_result_t** out, int64_t* products);
+
+/* Algorithm 4.1 on the stored values of A with bound eps_g and tolerance e_r:
+ * keeps the entries with |v| > t, t the final eps_f.  Writes t, the number of
+ * passes and the dropped F-norm b. */
+int sexpm_filter(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_iters, void* stream,
+                 sexpm_result_t** out, double* t, int32_t* iters, double* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEXPM_H_ */

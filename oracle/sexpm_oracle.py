@@ -185,6 +185,7 @@ class TaylorTerm:
     nnz: int
     t: float
     iters: int
+    products: int = 0
 
 
 @dataclasses.dataclass
@@ -197,6 +198,7 @@ class SquareStep:
     t: float
     iters: int
     b: float
+    products: int = 0
 
 
 @dataclasses.dataclass
@@ -213,6 +215,11 @@ class OracleStats:
     steps: List[SquareStep]
     nnz_T0: int = 0
     nnz_out: int = 0
+
+
+def product_count(A: sp.csr_matrix, B: sp.csr_matrix) -> int:
+    """Number of scalar multiplications a_ik b_kj in the row-wise product A B (bookkeeping)."""
+    return int(np.diff(B.indptr)[A.indices].sum()) if A.nnz else 0
 
 
 def _canon(A) -> sp.csr_matrix:
@@ -233,10 +240,11 @@ def taylor_phase(H0: sp.csr_matrix, M: int, eps_g0: float, e_r: float, max_iter:
     terms: List[TaylorTerm] = []
     kept = [S.copy()] if keep_terms else None
     for i in range(2, M + 1):
+        prev = S
         St = _canon(S @ H0)
         St.data = St.data / i          # S~_i = S^_{i-1} H_0 / i
         S, info = filter_csr(St, eps_g0, e_r, max_iter)
-        terms.append(TaylorTerm(i, St.nnz, S.nnz, info.t, info.iters))
+        terms.append(TaylorTerm(i, St.nnz, S.nnz, info.t, info.iters, product_count(prev, H0)))
         if S.nnz == 0:
             break
         if keep_terms:
@@ -263,11 +271,12 @@ def squaring_phase(T0: sp.csr_matrix, N: int, a: float, r0: float, e_r: float, s
     iterates = [T0.copy()] if keep_iterates else None
     for i in range(1, N + 1):
         ri = math.ldexp(r0, i)                 # r_i = 2 r_{i-1}
+        Tprev = T
         Tt = square_raw(T)
         normF = norm_I_plus(Tt) if scale == "rel" else 1.0
         eps_g = a * ri * normF
         T, info = filter_csr(Tt, eps_g, e_r, max_iter)
-        steps.append(SquareStep(i, eps_g, normF, Tt.nnz, T.nnz, info.t, info.iters, info.b))
+        steps.append(SquareStep(i, eps_g, normF, Tt.nnz, T.nnz, info.t, info.iters, info.b, product_count(Tprev, Tprev)))
         if keep_iterates:
             iterates.append(T.copy())
     return T, steps, iterates

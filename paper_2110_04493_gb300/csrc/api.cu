@@ -1,0 +1,595 @@
+// C ABI and host driver of Algorithm 4.2 (filtered incremental scaling and squaring).
+//
+// The driver runs on the host and sequences device kernels on one stream:
+//   step 1  ||tau H||_F (device reduction) and (M, N) by Eq. (4.20) on the host;
+//   step 2  a = 1/(N+1) for normal H, else 1/||H||_F;
+//   step 3  H_0 = tau H 2^-N, the filtered Taylor terms S^_i of Eq. (4.11), T^_0 = sum S^_i;
+//   step 4  N squarings T~_i = 2 T^_{i-1} + T^_{i-1}^2, each filtered by Algorithm 4.1;
+//   step 5  e^{tau H} = I + T^_N.
+// Algorithm 4.1 is a host loop over device reduction passes: each pass returns one
+// scalar (the F-norm of the candidate dropped part) and the next eps_f is computed on
+// the host exactly as the algorithm states.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sexpm_internal.cuh"
+
+namespace sexpm {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  cudaGetLastError();  // clear a sticky launch error where possible
+  if (e == cudaErrorMemoryAllocation) fail(SEXPM_ENOMEM, std::string("out of device memory in ") + what);
+  fail(SEXPM_ECUDA, std::string(cudaGetErrorString(e)) + " in " + what);
+}
+
+// ---------------------------------------------------------------- pool
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+std::atomic<int64_t> g_live{0}, g_peak{0};
+
+cudaMemPool_t pool_for_current_device() {
+  int dev = 0;
+  SX_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) fail(SEXPM_ECUDA, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    SX_CUDA(cudaMemPoolCreate(&g_pools[dev], &props));
+    uint64_t thr = std::numeric_limits<uint64_t>::max();
+    SX_CUDA(cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &thr));
+  }
+  return g_pools[dev];
+}
+}  // namespace
+
+void* Pool::alloc(size_t bytes, cudaStream_t s) {
+  void* p = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool_for_current_device(), s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? SEXPM_ENOMEM : SEXPM_ECUDA,
+         "device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  const int64_t now = g_live.fetch_add((int64_t)bytes) + (int64_t)bytes;
+  int64_t pk = g_peak.load();
+  while (now > pk && !g_peak.compare_exchange_weak(pk, now)) {
+  }
+  return p;
+}
+
+void Pool::release(void* p, size_t bytes, cudaStream_t s) {
+  cudaFreeAsync(p, s);
+  g_live.fetch_sub((int64_t)bytes);
+}
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t k) { g_launches.fetch_add(k); }
+int64_t launches() { return g_launches.load(); }
+
+int64_t Pool::live() { return g_live.load(); }
+int64_t Pool::peak() { return g_peak.load(); }
+void Pool::reset_peak() { g_peak.store(g_live.load()); }
+
+// ---------------------------------------------------------------- helpers
+namespace {
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    SX_CUDA(cudaEventCreate(&a));
+    SX_CUDA(cudaEventCreate(&b));
+    SX_CUDA(cudaEventRecord(a, s));
+  }
+  ~Timer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  double ms() {
+    SX_CUDA(cudaEventRecord(b, s));
+    SX_CUDA(cudaEventSynchronize(b));
+    float m = 0.f;
+    SX_CUDA(cudaEventElapsedTime(&m, a, b));
+    return m;
+  }
+};
+
+void validate_host_csr(const sexpm_csr_view& H) {
+  if (H.n < 0 || H.nnz < 0 || H.n > INT32_MAX) fail(SEXPM_EINVAL, "bad dimensions");
+  if (H.n > 0 && (!H.row_ptr || (H.nnz > 0 && (!H.col || !H.val)))) fail(SEXPM_EINVAL, "null CSR array");
+  if (H.n == 0) return;
+  if (H.row_ptr[0] != 0 || H.row_ptr[H.n] != H.nnz) fail(SEXPM_EINVAL, "row_ptr must start at 0 and end at nnz");
+  for (int64_t i = 0; i < H.n; ++i) {
+    const int64_t p0 = H.row_ptr[i], p1 = H.row_ptr[i + 1];
+    if (p1 < p0 || p1 > H.nnz) fail(SEXPM_EINVAL, "row_ptr not monotone at row " + std::to_string(i));
+    int32_t prev = -1;
+    for (int64_t p = p0; p < p1; ++p) {
+      const int32_t c = H.col[p];
+      if (c <= prev || c >= H.n) fail(SEXPM_EINVAL, "columns unsorted, duplicated or out of range in row " + std::to_string(i));
+      if (!std::isfinite(H.val[p])) fail(SEXPM_EINVAL, "non-finite value in row " + std::to_string(i));
+      prev = c;
+    }
+  }
+}
+
+// Copy a borrowed view (host or device) into an owned device CSR.
+void upload(const sexpm_csr_view& V, cudaStream_t s, CsrOwned& out, HostScalars& hs) {
+  if (!V.on_device) validate_host_csr(V);
+  out.n = V.n;
+  out.nnz = V.nnz;
+  out.rp.reset(V.n + 1, s);
+  out.ci.reset(V.nnz, s);
+  out.v.reset(V.nnz, s);
+  const cudaMemcpyKind k = V.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (V.n >= 0 && V.row_ptr) SX_CUDA(cudaMemcpyAsync(out.rp.p, V.row_ptr, (V.n + 1) * sizeof(int64_t), k, s));
+  if (V.nnz) {
+    SX_CUDA(cudaMemcpyAsync(out.ci.p, V.col, V.nnz * sizeof(int32_t), k, s));
+    SX_CUDA(cudaMemcpyAsync(out.v.p, V.val, V.nnz * sizeof(double), k, s));
+  }
+  if (V.on_device) {
+    if (V.n < 0 || V.nnz < 0 || V.n > INT32_MAX) fail(SEXPM_EINVAL, "bad dimensions");
+    if (!csr_valid(out.view(), s, hs)) fail(SEXPM_EINVAL, "invalid device CSR (row_ptr, column order/range or non-finite value)");
+  }
+}
+
+struct FilterOut {
+  double t = 0.0, b = 0.0;
+  int iters = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
+};
+
+// Algorithm 4.1 on the stored values of A, then A~ = A - b_n into `out`.
+FilterOut filter_alg41(const CsrD& A, double eps_g, double e_r, int max_iters, cudaStream_t s, CsrOwned& out,
+                       HostScalars& hs) {
+  FilterOut r;
+  Timer tf(s);
+  DevBuf<int32_t> keep(A.n ? A.n : 1, s);
+  double m = 1.0;
+  double b = std::numeric_limits<double>::infinity();  // the first pass always runs
+  double eps_f = eps_g;
+  int n = 0;
+  while (b > eps_g * (1.0 + e_r)) {
+    if (n >= max_iters) fail(SEXPM_ENOCONV, "Algorithm 4.1 did not converge within " + std::to_string(max_iters) + " passes");
+    eps_f = eps_g / m;
+    b = std::sqrt(filter_pass(A, eps_f, keep.p, s, hs));
+    m = b / eps_f;
+    ++n;
+  }
+  out.n = A.n;
+  out.rp.reset(A.n + 1, s);
+  out.nnz = scan_counts(keep.p, A.n, out.rp.p, s, hs);
+  out.ci.reset(out.nnz, s);
+  out.v.reset(out.nnz, s);
+  compact(A, eps_f, out, s);
+  r.t = eps_f;
+  r.b = b;
+  r.iters = n;
+  r.ms = tf.ms();
+  const double nr = (double)A.n + 1.0;
+  r.bytes = n * (8.0 * A.nnz + 8.0 * nr + 4.0 * A.n) + (4.0 * A.n + 8.0 * nr) +
+            (12.0 * A.nnz + 16.0 * nr + 12.0 * out.nnz);
+  return r;
+}
+
+void copy_csr(const CsrD& A, cudaStream_t s, CsrOwned& out) {
+  out.n = A.n;
+  out.nnz = A.nnz;
+  out.rp.reset(A.n + 1, s);
+  out.ci.reset(A.nnz, s);
+  out.v.reset(A.nnz, s);
+  SX_CUDA(cudaMemcpyAsync(out.rp.p, A.rp, (A.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  if (A.nnz) {
+    SX_CUDA(cudaMemcpyAsync(out.ci.p, A.ci, A.nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    SX_CUDA(cudaMemcpyAsync(out.v.p, A.v, A.nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+}  // namespace
+}  // namespace sexpm
+
+using namespace sexpm;
+
+struct sexpm_plan {
+  int device = 0;
+  cudaStream_t s = nullptr;
+  sexpm_options opt;
+  double eps = 0.0;
+  CsrOwned H;
+  int normal = 1;
+  HostScalars hs;
+};
+
+struct sexpm_result {
+  cudaStream_t s = nullptr;
+  CsrOwned E;
+  sexpm_stats_t st;
+  std::vector<sexpm_step_stats> steps;
+};
+
+#define SX_API_BEGIN try {
+#define SX_API_END                                         \
+  }                                                        \
+  catch (const sexpm::Error& e) {                          \
+    set_last_error(e.msg);                                 \
+    return e.code;                                         \
+  }                                                        \
+  catch (const std::bad_alloc&) {                          \
+    set_last_error("host allocation failed");              \
+    return SEXPM_ENOMEM;                                   \
+  }                                                        \
+  catch (...) {                                            \
+    set_last_error("unexpected exception");                \
+    return SEXPM_ECUDA;                                    \
+  }                                                        \
+  set_last_error("");                                      \
+  return SEXPM_OK;
+
+extern "C" {
+
+const char* sexpm_last_error(void) { return g_last_error.c_str(); }
+
+int64_t sexpm_kernel_launches(void) { return launches(); }
+
+int sexpm_release_memory(void) {
+  SX_API_BEGIN
+  SX_CUDA(cudaDeviceSynchronize());
+  SX_CUDA(cudaMemPoolTrimTo(pool_for_current_device(), 0));
+  SX_API_END
+}
+
+int sexpm_options_default(sexpm_options* opt) {
+  if (!opt) return SEXPM_EINVAL;
+  opt->e_r = 0.1;
+  opt->square_scale = 1;
+  opt->normal_override = -1;
+  opt->max_filter_iters = 100;
+  opt->n_extra = 50;
+  opt->max_taylor = 1000;
+  return SEXPM_OK;
+}
+
+static void check_options(const sexpm_options& o) {
+  if (!(o.e_r > 0.0) || !std::isfinite(o.e_r)) fail(SEXPM_EINVAL, "e_r must be positive and finite");
+  if (o.square_scale != 0 && o.square_scale != 1) fail(SEXPM_EINVAL, "square_scale must be 0 or 1");
+  if (o.normal_override < -1 || o.normal_override > 1) fail(SEXPM_EINVAL, "normal_override must be -1, 0 or 1");
+  if (o.max_filter_iters < 1 || o.n_extra < 0 || o.max_taylor < 1) fail(SEXPM_EINVAL, "bad iteration limits");
+}
+
+int sexpm_plan(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_options* opt, void* stream,
+               sexpm_plan_t** out) {
+  SX_API_BEGIN
+  if (!H || !out) fail(SEXPM_EINVAL, "null argument");
+  *out = nullptr;
+  if (H->n != n) fail(SEXPM_EINVAL, "n does not match the matrix dimension");
+  if (!(eps > 0.0) || !std::isfinite(eps)) fail(SEXPM_EINVAL, "eps must be positive and finite");
+  sexpm_plan_t* p = new sexpm_plan_t();
+  try {
+    if (opt) p->opt = *opt; else sexpm_options_default(&p->opt);
+    check_options(p->opt);
+    SX_CUDA(cudaGetDevice(&p->device));
+    p->s = static_cast<cudaStream_t>(stream);
+    p->eps = eps;
+    upload(*H, p->s, p->H, p->hs);
+    if (p->opt.normal_override >= 0) {
+      p->normal = p->opt.normal_override;
+    } else {
+      // Algorithm 4.2 step 2: normality.  Exact symmetry / skew-symmetry first.
+      CsrOwned Ht;
+      transpose(p->H.view(), p->s, Ht, p->hs);
+      if (csr_equal(p->H.view(), Ht.view(), 1.0, p->s, p->hs) || csr_equal(p->H.view(), Ht.view(), -1.0, p->s, p->hs)) {
+        p->normal = 1;
+      } else {
+        CsrOwned P, Q, C;
+        CsrD none;
+        spgemm(p->H.view(), Ht.view(), none, 1.0, 0.0, p->s, P, nullptr, p->hs);
+        spgemm(Ht.view(), p->H.view(), none, 1.0, 0.0, p->s, Q, nullptr, p->hs);
+        add(P.view(), Q.view(), -1.0, p->s, C, p->hs);
+        const double nc = std::sqrt(sum_squares(C.view(), p->s, p->hs));
+        const double nh2 = sum_squares(p->H.view(), p->s, p->hs);
+        p->normal = nc <= 64.0 * std::ldexp(1.0, -53) * nh2 ? 1 : 0;
+      }
+    }
+    SX_CUDA(cudaStreamSynchronize(p->s));
+  } catch (...) {
+    delete p;
+    throw;
+  }
+  *out = p;
+  SX_API_END
+}
+
+int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
+  SX_API_BEGIN
+  if (!p || !out) fail(SEXPM_EINVAL, "null argument");
+  *out = nullptr;
+  if (!std::isfinite(tau)) fail(SEXPM_EINVAL, "tau must be finite");
+  int dev = 0;
+  SX_CUDA(cudaGetDevice(&dev));
+  if (dev != p->device) fail(SEXPM_EINVAL, "current device differs from the plan's device");
+  cudaStream_t s = p->s;
+  HostScalars& hs = p->hs;
+  const sexpm_options& o = p->opt;
+  const int64_t n = p->H.n;
+  sexpm_result* res = new sexpm_result();
+  try {
+    res->s = s;
+    std::memset(&res->st, 0, sizeof(res->st));
+    sexpm_stats_t& st = res->st;
+    st.n = n;
+    Pool::reset_peak();
+    const int64_t live0 = Pool::live();
+    const int64_t launches0 = launches();
+    Timer t_all(s);
+    // step 1: tau H and its F-norm, (M, N)
+    CsrD Hs = p->H.view();
+    DevBuf<double> hv(p->H.nnz, s);
+    scale_values(p->H.v.p, tau, p->H.nnz, hv.p, s);
+    Hs.v = hv.p;
+    const double normH = std::sqrt(sum_squares(Hs, s, hs));
+    st.norm_H = normH;
+    int32_t M = 0, N = 0;
+    const int rc = sexpm_choose_MN(normH, p->eps, o.n_extra, o.max_taylor, &M, &N);
+    if (rc != SEXPM_OK) fail(rc, rc == SEXPM_ENOPARAM ? "no feasible (M, N) for this tolerance" : "invalid (M, N) input");
+    st.M = M;
+    st.N = N;
+    const bool normal = (p->normal != 0) || normH == 0.0;
+    st.normal = normal ? 1 : 0;
+    if (M == 0) {
+      // ||tau H|| = 0: e^0 = I
+      CsrOwned Z;
+      Z.n = n;
+      Z.nnz = 0;
+      Z.rp.reset(n + 1, s);
+      SX_CUDA(cudaMemsetAsync(Z.rp.p, 0, (n + 1) * sizeof(int64_t), s));
+      add_identity(Z.view(), s, res->E, hs);
+      st.nnz_out = res->E.nnz;
+      st.ms_total = t_all.ms();
+      st.peak_bytes = Pool::peak() - live0;
+      st.launches = launches() - launches0;
+      *out = res;
+      set_last_error("");
+      return SEXPM_OK;
+    }
+    // step 2: filter parameter a
+    const double a = normal ? 1.0 / (1.0 + N) : 1.0 / normH;
+    st.a = a;
+    // step 3: Taylor phase on H_0 = tau H 2^-N
+    Timer t_tay(s);
+    DevBuf<double> h0v(p->H.nnz, s);
+    scale_values(hv.p, std::ldexp(1.0, -N), p->H.nnz, h0v.p, s);
+    CsrD H0 = Hs;
+    H0.v = h0v.p;
+    const double x0 = std::ldexp(normH, -N);
+    const double r0 = sexpm_rho(M, x0);
+    const double eps_g0 = a * r0 / ((double)M * std::exp(2.0 * x0));
+    st.r0 = r0;
+    st.eps_g0 = eps_g0;
+    CsrOwned T;       // running T^_0, later T^_i
+    copy_csr(H0, s, T);
+    CsrOwned S;       // current filtered term (S_1 = H_0 is not filtered)
+    CsrD Sv = H0;
+    CsrD none;
+    for (int i = 2; i <= M; ++i) {
+      Timer ts(s);
+      CsrOwned St;
+      SpgemmTimes tm;
+      const int64_t prod = spgemm(Sv, H0, none, (double)i, 0.0, s, St, nullptr, hs, &tm);
+      CsrOwned Sn;
+      FilterOut fo = filter_alg41(St.view(), eps_g0, o.e_r, o.max_filter_iters, s, Sn, hs);
+      sexpm_step_stats rec;
+      std::memset(&rec, 0, sizeof(rec));
+      rec.phase = 0;
+      rec.i = i;
+      rec.iters = fo.iters;
+      rec.eps_g = eps_g0;
+      rec.t = fo.t;
+      rec.b = fo.b;
+      rec.nnz_raw = St.nnz;
+      rec.nnz = Sn.nnz;
+      rec.products = prod;
+      rec.ms_symbolic = tm.ms_symbolic;
+      rec.ms_numeric = tm.ms_numeric;
+      rec.ms_filter = fo.ms;
+      rec.flops = 2.0 * (double)prod + (double)St.nnz;
+      rec.bytes_filter = fo.bytes;
+      if (Sn.nnz == 0) {
+        rec.ms = ts.ms();
+        res->steps.push_back(rec);
+        break;
+      }
+      CsrOwned Tn;
+      add(T.view(), Sn.view(), 1.0, s, Tn, hs);
+      T = std::move(Tn);
+      S = std::move(Sn);
+      Sv = S.view();
+      rec.ms = ts.ms();
+      res->steps.push_back(rec);
+    }
+    S.rp.free(); S.ci.free(); S.v.free();
+    st.ms_taylor = t_tay.ms();
+    // step 4: N filtered squarings
+    Timer t_sq(s);
+    RowStats rs;
+    for (int i = 1; i <= N; ++i) {
+      Timer ts(s);
+      const double ri = std::ldexp(r0, i);
+      CsrOwned Tt;
+      SpgemmTimes tm;
+      const int64_t prod = spgemm(T.view(), T.view(), T.view(), 1.0, 2.0, s, Tt, &rs, hs, &tm);
+      const double flops = 2.0 * (double)prod + 2.0 * (double)T.nnz;
+      double normF = 1.0;
+      if (o.square_scale) {
+        const double sq = reduce_sum(rs.sq.p, n, s, hs);
+        const double tr = reduce_sum(rs.diag.p, n, s, hs);
+        const double f2 = sq + (double)n + 2.0 * tr;
+        normF = std::sqrt(f2 > 0.0 ? f2 : 0.0);
+      }
+      const double eps_g = a * ri * normF;
+      T.rp.free(); T.ci.free(); T.v.free();
+      CsrOwned Tn;
+      FilterOut fo = filter_alg41(Tt.view(), eps_g, o.e_r, o.max_filter_iters, s, Tn, hs);
+      sexpm_step_stats rec;
+      std::memset(&rec, 0, sizeof(rec));
+      rec.phase = 1;
+      rec.i = i;
+      rec.iters = fo.iters;
+      rec.eps_g = eps_g;
+      rec.t = fo.t;
+      rec.b = fo.b;
+      rec.norm_F = o.square_scale ? normF : 0.0;
+      rec.nnz_raw = Tt.nnz;
+      rec.nnz = Tn.nnz;
+      rec.products = prod;
+      rec.ms_symbolic = tm.ms_symbolic;
+      rec.ms_numeric = tm.ms_numeric;
+      rec.ms_filter = fo.ms;
+      rec.flops = flops;
+      rec.bytes_filter = fo.bytes;
+      Tt.rp.free(); Tt.ci.free(); Tt.v.free();
+      T = std::move(Tn);
+      rec.ms = ts.ms();
+      res->steps.push_back(rec);
+    }
+    st.ms_squaring = t_sq.ms();
+    // step 5: e^{tau H} = I + T^_N
+    Timer t_fin(s);
+    add_identity(T.view(), s, res->E, hs);
+    st.ms_final = t_fin.ms();
+    st.nnz_out = res->E.nnz;
+    st.n_steps = (int32_t)res->steps.size();
+    st.ms_total = t_all.ms();
+    st.peak_bytes = Pool::peak() - live0;
+    st.launches = launches() - launches0;
+  } catch (...) {
+    delete res;
+    throw;
+  }
+  *out = res;
+  SX_API_END
+}
+
+int sexpm_result_info(const sexpm_result_t* r, int64_t* n, int64_t* nnz) {
+  if (!r) {
+    set_last_error("null result");
+    return SEXPM_EINVAL;
+  }
+  if (n) *n = r->E.n;
+  if (nnz) *nnz = r->E.nnz;
+  return SEXPM_OK;
+}
+
+int sexpm_result_copy(const sexpm_result_t* r, int64_t* row_ptr, int32_t* col, double* val, int32_t on_device) {
+  SX_API_BEGIN
+  if (!r) fail(SEXPM_EINVAL, "null result");
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (row_ptr) SX_CUDA(cudaMemcpyAsync(row_ptr, r->E.rp.p, (r->E.n + 1) * sizeof(int64_t), k, r->s));
+  if (r->E.nnz) {
+    if (col) SX_CUDA(cudaMemcpyAsync(col, r->E.ci.p, r->E.nnz * sizeof(int32_t), k, r->s));
+    if (val) SX_CUDA(cudaMemcpyAsync(val, r->E.v.p, r->E.nnz * sizeof(double), k, r->s));
+  }
+  SX_CUDA(cudaStreamSynchronize(r->s));
+  SX_API_END
+}
+
+int sexpm_stats(const sexpm_result_t* r, sexpm_stats_t* stats, sexpm_step_stats* steps, int32_t max_steps) {
+  if (!r || !stats) {
+    set_last_error("null argument");
+    return SEXPM_EINVAL;
+  }
+  *stats = r->st;
+  stats->n_steps = (int32_t)r->steps.size();
+  if (steps)
+    for (int32_t k = 0; k < max_steps && k < (int32_t)r->steps.size(); ++k) steps[k] = r->steps[k];
+  return SEXPM_OK;
+}
+
+void sexpm_result_free(sexpm_result_t* r) { delete r; }
+
+void sexpm_plan_destroy(sexpm_plan_t* p) { delete p; }
+
+int sexpm_spgemm(const sexpm_csr_view* A, const sexpm_csr_view* B, const sexpm_csr_view* D, double div, double beta,
+                 void* stream, sexpm_result_t** out, int64_t* products) {
+  SX_API_BEGIN
+  if (!A || !B || !out) fail(SEXPM_EINVAL, "null argument");
+  *out = nullptr;
+  if (A->n != B->n || (D && D->n != A->n)) fail(SEXPM_EINVAL, "dimension mismatch");
+  if (!(div != 0.0) || !std::isfinite(div) || !std::isfinite(beta)) fail(SEXPM_EINVAL, "div must be finite and nonzero, beta finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostScalars hs;
+  CsrOwned a, b, d;
+  upload(*A, s, a, hs);
+  upload(*B, s, b, hs);
+  CsrD dv;
+  if (D) {
+    upload(*D, s, d, hs);
+    dv = d.view();
+  }
+  sexpm_result* res = new sexpm_result();
+  try {
+    res->s = s;
+    std::memset(&res->st, 0, sizeof(res->st));
+    const int64_t prod = spgemm(a.view(), b.view(), dv, div, beta, s, res->E, nullptr, hs);
+    SX_CUDA(cudaStreamSynchronize(s));
+    res->st.n = res->E.n;
+    res->st.nnz_out = res->E.nnz;
+    if (products) *products = prod;
+  } catch (...) {
+    delete res;
+    throw;
+  }
+  *out = res;
+  SX_API_END
+}
+
+int sexpm_filter(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_iters, void* stream,
+                 sexpm_result_t** out, double* t, int32_t* iters, double* b) {
+  SX_API_BEGIN
+  if (!A || !out) fail(SEXPM_EINVAL, "null argument");
+  *out = nullptr;
+  if (!(eps_g >= 0.0) || !std::isfinite(eps_g) || !(e_r > 0.0) || !std::isfinite(e_r) || max_iters < 1)
+    fail(SEXPM_EINVAL, "bad filter parameters");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostScalars hs;
+  CsrOwned a;
+  upload(*A, s, a, hs);
+  sexpm_result* res = new sexpm_result();
+  try {
+    res->s = s;
+    std::memset(&res->st, 0, sizeof(res->st));
+    FilterOut fo = filter_alg41(a.view(), eps_g, e_r, max_iters, s, res->E, hs);
+    SX_CUDA(cudaStreamSynchronize(s));
+    res->st.n = res->E.n;
+    res->st.nnz_out = res->E.nnz;
+    if (t) *t = fo.t;
+    if (iters) *iters = fo.iters;
+    if (b) *b = fo.b;
+  } catch (...) {
+    delete res;
+    throw;
+  }
+  *out = res;
+  SX_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// Internal declarations shared by the translation units of libsexpm.
+// Device CSR layout: int64 row pointers, int32 sorted column indices, float64 values.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sexpm.h"
+
+namespace sexpm {
+
+// Non-owning device CSR view used by the kernels.
+struct CsrD {
+  int64_t n = 0;
+  int64_t nnz = 0;
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const double* v = nullptr;
+};
+
+// Error carried from deep inside the host driver up to the C ABI.
+struct Error {
+  int code;
+  std::string msg;
+};
+
+void set_last_error(const std::string& msg);
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define SX_CUDA(x) ::sexpm::check_cuda((x), #x)
+
+// ---------------------------------------------------------------- device memory
+// Stream-ordered allocations from a library-owned pool.  Tracks live and peak bytes.
+struct Pool {
+  static void* alloc(size_t bytes, cudaStream_t s);
+  static void release(void* p, size_t bytes, cudaStream_t s);
+  static int64_t live();
+  static int64_t peak();
+  static void reset_peak();
+};
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t count = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(size_t n, cudaStream_t st) { reset(n, st); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), count(o.count), s(o.s) { o.p = nullptr; o.count = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      free();
+      p = o.p; count = o.count; s = o.s;
+      o.p = nullptr; o.count = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { free(); }
+  void reset(size_t n, cudaStream_t st) {
+    free();
+    s = st;
+    count = n;
+    p = n ? static_cast<T*>(Pool::alloc(n * sizeof(T), st)) : nullptr;
+  }
+  void free() {
+    if (p) Pool::release(p, count * sizeof(T), s);
+    p = nullptr;
+    count = 0;
+  }
+};
+
+// An owned device CSR matrix.
+struct CsrOwned {
+  int64_t n = 0;
+  int64_t nnz = 0;
+  DevBuf<int64_t> rp;
+  DevBuf<int32_t> ci;
+  DevBuf<double> v;
+  CsrD view() const {
+    CsrD d;
+    d.n = n; d.nnz = nnz; d.rp = rp.p; d.ci = ci.p; d.v = v.p;
+    return d;
+  }
+};
+
+// Per-row statistics written by the numeric product kernel.
+struct RowStats {
+  DevBuf<double> sq;    // sum of v^2 over the row
+  DevBuf<double> diag;  // value stored at (i, i), 0 if absent
+};
+
+// Small pinned host buffer used to read back scalars.
+struct HostScalars {
+  double* d = nullptr;
+  int64_t* i = nullptr;
+  HostScalars();
+  ~HostScalars();
+};
+
+// Number of kernels this library has enqueued (all launchers add to it).
+void count_launches(int64_t k);
+int64_t launches();
+
+// Device times of the phases of one sparse product (filled when requested).
+struct SpgemmTimes {
+  double ms_symbolic = 0.0;  // analysis, classification and the symbolic pass
+  double ms_numeric = 0.0;   // the numeric pass (products, fused scaling and beta D)
+};
+
+// ---------------------------------------------------------------- kernels (launchers)
+// All launchers enqueue on stream s and do not synchronise unless stated.
+
+// C = (A B) / div + beta D.  D may have n == 0 (absent).  Allocates C; fills row
+// statistics (sum of squares, diagonal) when stats != nullptr.  Synchronises s
+// once to size C.  Returns the number of scalar products.
+int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, cudaStream_t s,
+               CsrOwned& C, RowStats* stats, HostScalars& hs, SpgemmTimes* times = nullptr);
+
+// sum_i x[i] over n doubles, deterministic order.  Synchronises and returns the sum.
+double reduce_sum(const double* x, int64_t n, cudaStream_t s, HostScalars& hs);
+// sum over the stored values of A of v^2.
+double sum_squares(const CsrD& A, cudaStream_t s, HostScalars& hs);
+
+// One Algorithm 4.1 pass: returns sum_{|v| <= t} v^2 over the stored values of A and
+// writes keep[i] = #{ |v| > t } for every row.  Synchronises s.
+double filter_pass(const CsrD& A, double t, int32_t* keep, cudaStream_t s, HostScalars& hs);
+
+// Exclusive scan of int32 counts into int64 row pointers (n+1 entries).  Returns the total
+// (synchronises s).
+int64_t scan_counts(const int32_t* cnt, int64_t n, int64_t* rp, cudaStream_t s, HostScalars& hs);
+
+// Copy the entries of A with |v| > t into C (rows given by C.rp, already scanned).
+void compact(const CsrD& A, double t, CsrOwned& C, cudaStream_t s);
+
+// C = A + beta B (union pattern).
+void add(const CsrD& A, const CsrD& B, double beta, cudaStream_t s, CsrOwned& C, HostScalars& hs);
+
+// C = I + A (diagonal inserted where absent).
+void add_identity(const CsrD& A, cudaStream_t s, CsrOwned& C, HostScalars& hs);
+
+// y[k] = alpha x[k] (values only).
+void scale_values(const double* x, double alpha, int64_t n, double* y, cudaStream_t s);
+
+// A^T into T (columns sorted within rows).
+void transpose(const CsrD& A, cudaStream_t s, CsrOwned& T, HostScalars& hs);
+
+// Pattern and values of A and B equal (sign = +1) or B = -A (sign = -1)?  Synchronises s.
+bool csr_equal(const CsrD& A, const CsrD& B, double sign, cudaStream_t s, HostScalars& hs);
+
+// Validation on device: sorted unique in-range columns, finite values, monotone row_ptr.
+bool csr_valid(const CsrD& A, cudaStream_t s, HostScalars& hs);
+
+}  // namespace sexpm

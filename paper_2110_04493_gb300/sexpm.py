@@ -1,0 +1,313 @@
+"""Python binding of libsexpm (the C ABI declared in include/sexpm.h).
+
+Argument marshalling only: every step of the method runs inside the library's
+CUDA kernels.  PyTorch supplies device buffers and the current CUDA stream.
+The library must have been built (``python -m paper_2110_04493_gb300.build``);
+importing the binding without it raises immediately: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Any, Dict, List, Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsexpm.so")
+
+SEXPM_OK = 0
+ERROR_NAMES = {
+    -1: "SEXPM_EINVAL", -2: "SEXPM_ENOMEM", -3: "SEXPM_ECUDA", -4: "SEXPM_ENOCONV",
+    -5: "SEXPM_ENOPARAM", -6: "SEXPM_ETIMEOUT", -7: "SEXPM_EOVERFLOW",
+}
+
+
+class SexpmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class CsrView(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("e_r", ctypes.c_double), ("square_scale", ctypes.c_int32), ("normal_override", ctypes.c_int32),
+                ("max_filter_iters", ctypes.c_int32), ("n_extra", ctypes.c_int32), ("max_taylor", ctypes.c_int32)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("phase", ctypes.c_int32), ("i", ctypes.c_int32), ("iters", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("eps_g", ctypes.c_double), ("t", ctypes.c_double), ("b", ctypes.c_double),
+                ("norm_F", ctypes.c_double), ("nnz_raw", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("products", ctypes.c_int64), ("ms", ctypes.c_double), ("ms_symbolic", ctypes.c_double),
+                ("ms_numeric", ctypes.c_double), ("ms_filter", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes_filter", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("norm_H", ctypes.c_double), ("M", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("normal", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("a", ctypes.c_double),
+                ("r0", ctypes.c_double), ("eps_g0", ctypes.c_double), ("nnz_out", ctypes.c_int64),
+                ("ms_total", ctypes.c_double), ("ms_taylor", ctypes.c_double), ("ms_squaring", ctypes.c_double),
+                ("ms_final", ctypes.c_double), ("peak_bytes", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libsexpm.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built; run python -m paper_2110_04493_gb300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    L.sexpm_last_error.restype = ctypes.c_char_p
+    L.sexpm_options_default.argtypes = [P(Options)]
+    L.sexpm_plan.argtypes = [P(CsrView), ctypes.c_int64, ctypes.c_double, P(Options), vp, P(vp)]
+    L.sexpm_compute.argtypes = [vp, ctypes.c_double, P(vp)]
+    L.sexpm_result_info.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64)]
+    L.sexpm_result_copy.argtypes = [vp, vp, vp, vp, ctypes.c_int32]
+    L.sexpm_stats.argtypes = [vp, P(Stats), P(StepStats), ctypes.c_int32]
+    L.sexpm_result_free.argtypes = [vp]
+    L.sexpm_result_free.restype = None
+    L.sexpm_plan_destroy.argtypes = [vp]
+    L.sexpm_plan_destroy.restype = None
+    L.sexpm_kernel_launches.restype = ctypes.c_int64
+    L.sexpm_kernel_launches.argtypes = []
+    L.sexpm_release_memory.argtypes = []
+    L.sexpm_rho.argtypes = [ctypes.c_int32, ctypes.c_double]
+    L.sexpm_rho.restype = ctypes.c_double
+    L.sexpm_choose_MN.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                  P(ctypes.c_int32), P(ctypes.c_int32)]
+    L.sexpm_spgemm.argtypes = [P(CsrView), P(CsrView), P(CsrView), ctypes.c_double, ctypes.c_double, vp, P(vp),
+                               P(ctypes.c_int64)]
+    L.sexpm_filter.argtypes = [P(CsrView), ctypes.c_double, ctypes.c_double, ctypes.c_int32, vp, P(vp),
+                               P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_double)]
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> None:
+    if rc != SEXPM_OK:
+        raise SexpmError(rc, load().sexpm_last_error().decode())
+
+
+def _stream_ptr(stream=None) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ views
+
+def _arrays(H) -> Tuple[Any, Any, Any, int]:
+    """Accepts (row_ptr, col, val[, n]) tuples or objects with row_ptr/col/val/n attributes."""
+    if isinstance(H, (tuple, list)):
+        rp, ci, v = H[0], H[1], H[2]
+        n = H[3] if len(H) > 3 else len(rp) - 1
+    else:
+        rp, ci, v, n = H.row_ptr, H.col, H.val, H.n
+    return rp, ci, v, int(n)
+
+
+def _make_view(H, keep: List[Any]) -> CsrView:
+    rp, ci, v, n = _arrays(H)
+    try:
+        import torch
+        is_t = isinstance(rp, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        is_t = False
+    if is_t:
+        on_dev = rp.is_cuda
+        rp = rp.to(dtype=torch.int64).contiguous()
+        ci = ci.to(dtype=torch.int32).contiguous()
+        v = v.to(dtype=torch.float64).contiguous()
+        if not (rp.is_cuda == ci.is_cuda == v.is_cuda):
+            raise ValueError("row_ptr, col and val must live on the same device")
+        keep += [rp, ci, v]
+        ptrs = (rp.data_ptr(), ci.data_ptr() if ci.numel() else None, v.data_ptr() if v.numel() else None)
+        nnz = int(ci.numel())
+    else:
+        rp = np.ascontiguousarray(rp, dtype=np.int64)
+        ci = np.ascontiguousarray(ci, dtype=np.int32)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        keep += [rp, ci, v]
+        on_dev = False
+        ptrs = (rp.ctypes.data, ci.ctypes.data if ci.size else None, v.ctypes.data if v.size else None)
+        nnz = int(ci.size)
+    return CsrView(n, nnz, ptrs[0], ptrs[1], ptrs[2], 1 if on_dev else 0)
+
+
+def options(**kw) -> Options:
+    o = Options()
+    _check(load().sexpm_options_default(ctypes.byref(o)))
+    for k, val in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, val)
+    return o
+
+
+# ------------------------------------------------------------------ results
+
+class Result:
+    """A library-owned device CSR result."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    def info(self) -> Tuple[int, int]:
+        n, nnz = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().sexpm_result_info(self._h, ctypes.byref(n), ctypes.byref(nnz)))
+        return n.value, nnz.value
+
+    def to_torch(self, device="cuda"):
+        import torch
+        n, nnz = self.info()
+        rp = torch.empty(n + 1, dtype=torch.int64, device=device)
+        ci = torch.empty(nnz, dtype=torch.int32, device=device)
+        v = torch.empty(nnz, dtype=torch.float64, device=device)
+        on_dev = 1 if rp.is_cuda else 0
+        if on_dev:
+            torch.cuda.current_stream().synchronize()
+        _check(load().sexpm_result_copy(self._h, rp.data_ptr(), ci.data_ptr() if nnz else None,
+                                        v.data_ptr() if nnz else None, on_dev))
+        return rp, ci, v
+
+    def to_numpy(self):
+        n, nnz = self.info()
+        rp = np.empty(n + 1, dtype=np.int64)
+        ci = np.empty(nnz, dtype=np.int32)
+        v = np.empty(nnz, dtype=np.float64)
+        _check(load().sexpm_result_copy(self._h, rp.ctypes.data, ci.ctypes.data if nnz else None,
+                                        v.ctypes.data if nnz else None, 0))
+        return rp, ci, v
+
+    def stats(self) -> Dict[str, Any]:
+        st = Stats()
+        steps = (StepStats * 512)()
+        _check(load().sexpm_stats(self._h, ctypes.byref(st), steps, 512))
+        d = {f: getattr(st, f) for f, _ in Stats._fields_}
+        d["steps"] = [{f: getattr(steps[k], f) for f, _ in StepStats._fields_ if f != "pad_"}
+                      for k in range(min(st.n_steps, 512))]
+        return d
+
+    def free(self) -> None:
+        if self._h:
+            load().sexpm_result_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Plan:
+    """sexpm_plan: H copied to the device, ||H||_F and normality computed on the GPU."""
+
+    def __init__(self, H, eps: float, stream=None, **opts):
+        keep: List[Any] = []
+        view = _make_view(H, keep)
+        self._stream = _stream_ptr(stream)
+        h = ctypes.c_void_p()
+        o = options(**opts)
+        _check(load().sexpm_plan(ctypes.byref(view), view.n, float(eps), ctypes.byref(o), self._stream,
+                                 ctypes.byref(h)))
+        self._h = h
+        self.n = view.n
+
+    def compute(self, tau: float = 1.0) -> Result:
+        r = ctypes.c_void_p()
+        _check(load().sexpm_compute(self._h, float(tau), ctypes.byref(r)))
+        return Result(r.value)
+
+    def close(self) -> None:
+        if self._h:
+            load().sexpm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def expm(H, tau: float = 1.0, eps: float = 1e-12, device="cuda", **opts):
+    """e^{tau H} as (row_ptr, col, val) torch tensors on `device`, plus the stats dict."""
+    plan = Plan(H, eps, **opts)
+    try:
+        res = plan.compute(tau)
+        try:
+            out = res.to_torch(device)
+            st = res.stats()
+        finally:
+            res.free()
+    finally:
+        plan.close()
+    return out, st
+
+
+def spgemm(A, B, D=None, div: float = 1.0, beta: float = 0.0, device="cuda"):
+    """C = (A B)/div + beta D through sexpm_spgemm; returns ((row_ptr, col, val), products)."""
+    keep: List[Any] = []
+    a, b = _make_view(A, keep), _make_view(B, keep)
+    d = _make_view(D, keep) if D is not None else None
+    r = ctypes.c_void_p()
+    prod = ctypes.c_int64()
+    _check(load().sexpm_spgemm(ctypes.byref(a), ctypes.byref(b), ctypes.byref(d) if d is not None else None,
+                               float(div), float(beta), _stream_ptr(), ctypes.byref(r), ctypes.byref(prod)))
+    res = Result(r.value)
+    try:
+        return res.to_torch(device), prod.value
+    finally:
+        res.free()
+
+
+def filter_csr(A, eps_g: float, e_r: float = 0.1, max_iters: int = 100, device="cuda"):
+    """Algorithm 4.1 through sexpm_filter; returns ((row_ptr, col, val), t, iters, b)."""
+    keep: List[Any] = []
+    a = _make_view(A, keep)
+    r = ctypes.c_void_p()
+    t, it, b = ctypes.c_double(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().sexpm_filter(ctypes.byref(a), float(eps_g), float(e_r), int(max_iters), _stream_ptr(),
+                               ctypes.byref(r), ctypes.byref(t), ctypes.byref(it), ctypes.byref(b)))
+    res = Result(r.value)
+    try:
+        return res.to_torch(device), t.value, it.value, b.value
+    finally:
+        res.free()
+
+
+def kernel_launches() -> int:
+    """Kernels enqueued by the library since it was loaded."""
+    return int(load().sexpm_kernel_launches())
+
+
+def release_memory() -> None:
+    """Return the library's cached device memory to the driver."""
+    _check(load().sexpm_release_memory())
+
+
+def rho(M: int, x: float) -> float:
+    """Eq. (4.5), evaluated by the library's host code."""
+    return load().sexpm_rho(int(M), float(x))
+
+
+def choose_MN(norm_H: float, eps: float, n_extra: int = 50, max_M: int = 1000) -> Tuple[int, int]:
+    """Eq. (4.20), evaluated by the library's host code."""
+    M, N = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().sexpm_choose_MN(float(norm_H), float(eps), int(n_extra), int(max_M), ctypes.byref(M),
+                                  ctypes.byref(N)))
+    return M.value, N.value

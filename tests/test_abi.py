@@ -1,0 +1,88 @@
+"""CPU-only checks of the C ABI: the library loads, exports every declared symbol,
+and its host-side scalar code (Eq. 4.5, Eq. 4.20) matches the mathematics.
+No GPU call is made here."""
+import ctypes
+import decimal
+import math
+import os
+import re
+
+import pytest
+
+from oracle import sexpm_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sexpm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2110_04493_gb300 import build as B
+    B.build()
+    from paper_2110_04493_gb300 import sexpm
+    return sexpm.load()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sexpm_[a-z_A-Z0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ["sexpm_plan", "sexpm_compute", "sexpm_result_info", "sexpm_result_copy", "sexpm_stats",
+                     "sexpm_result_free", "sexpm_plan_destroy", "sexpm_last_error", "sexpm_spgemm", "sexpm_filter"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [f for f in _declared_functions() if not hasattr(lib, f)]
+    assert missing == []
+
+
+def test_options_default(lib):
+    from paper_2110_04493_gb300 import sexpm
+    o = sexpm.options()
+    assert (o.e_r, o.square_scale, o.normal_override, o.max_filter_iters, o.n_extra) == (0.1, 1, -1, 100, 50)
+
+
+def _rho_closed(M, x):
+    with decimal.localcontext() as ctx:
+        ctx.prec = 250
+        X = decimal.Decimal(repr(x))
+        s, term = decimal.Decimal(0), decimal.Decimal(1)
+        for k in range(M + 1):
+            if k:
+                term = term * (-X) / k
+            s += term
+        return float((X.exp() * s - 1) * (-1 if M % 2 else 1))
+
+
+@pytest.mark.parametrize("M,x", [(1, 0.5), (7, 0.0245), (15, 0.6), (20, 0.95664), (30, 1.0), (12, 2.5)])
+def test_host_rho_is_eq_4_5(lib, M, x):
+    from paper_2110_04493_gb300 import sexpm
+    assert sexpm.rho(M, x) == pytest.approx(_rho_closed(M, x), rel=1e-13)
+
+
+def test_host_choose_MN_reproduces_sec_5_2(lib):
+    from paper_2110_04493_gb300 import sexpm
+    assert sexpm.choose_MN(244.94489, 1e-16) == (20, 8)
+    assert sexpm.choose_MN(0.0, 1e-12) == (0, 0)
+
+
+def test_host_choose_MN_agrees_with_oracle_over_a_sweep(lib):
+    """Two independent codings of Eq. (4.20); the oracle's is pinned to the paper."""
+    from paper_2110_04493_gb300 import sexpm
+    for k in range(60):
+        normH = 10 ** (-3 + 9 * k / 59)
+        for eps in (1e-6, 1e-12, 1e-16):
+            assert sexpm.choose_MN(normH, eps) == O.choose_MN(normH, eps), (normH, eps)
+
+
+def test_host_choose_MN_rejects_bad_input(lib):
+    from paper_2110_04493_gb300 import sexpm
+    for bad in [(1.0, 0.0), (1.0, -1.0), (float("nan"), 1e-12), (1.0, float("inf"))]:
+        with pytest.raises(sexpm.SexpmError) as ei:
+            sexpm.choose_MN(*bad)
+        assert ei.value.code == -1

@@ -1,0 +1,230 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars: exact equality for the integer choices (M, N, normality) and the pattern of
+sparse products; element-wise |GPU - oracle| <= 1e-12 ||e^H||_1 for e^{tau H};
+entries stored by only one side must lie within a factor 2 of the drop threshold.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import sexpm_oracle as O
+from tests._compare import expm_parity, to_scipy, torch_csr
+from workloads import (
+    CSR,
+    diag_scale,
+    dirichlet_laplacian,
+    get_config,
+    paper_table1_matrices,
+    random_csr,
+    rgg_adjacency,
+    toeplitz_trid,
+)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sx():
+    from paper_2110_04493_gb300 import build as B
+    B.build()
+    from paper_2110_04493_gb300 import sexpm
+    sexpm.load()
+    return sexpm
+
+
+def _csr(M) -> CSR:
+    return CSR.from_scipy(sp.csr_matrix(M))
+
+
+# ------------------------------------------------------------------ the sparse product
+
+def _ragged(n, seed, dense_rows=(), empty_rows=()):
+    rng = np.random.default_rng(seed)
+    A = sp.random(n, n, density=min(1.0, 6.0 / n), random_state=np.random.RandomState(seed), format="lil")
+    for r in dense_rows:
+        cols = rng.choice(n, size=min(n, 3000), replace=False)
+        A[r, cols] = rng.uniform(-1, 1, size=len(cols))
+    for r in empty_rows:
+        A[r, :] = 0
+    A = sp.csr_matrix(A)
+    A.eliminate_zeros()
+    return A
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (7, 1), (300, 2), (5000, 3)])
+def test_spgemm_taylor_term_matches_scipy(sx, n, seed):
+    """S~ = S H_0 / i with a thin right operand (Eq. 4.10)."""
+    S = _ragged(n, seed, empty_rows=[0] if n > 1 else [])
+    H0 = _ragged(n, seed + 100)
+    (rp, ci, v), prod = sx.spgemm(torch_csr(_csr(S)), torch_csr(_csr(H0)), div=7.0)
+    G = to_scipy(rp, ci, v, n)
+    R = (S @ H0).tocsr()
+    R.data = R.data / 7.0
+    assert prod == int(sum(np.diff(H0.indptr)[S.indices]))
+    _assert_product_parity(G, R)
+
+
+@pytest.mark.parametrize("n,seed,dense", [(64, 4, ()), (2000, 5, (3, 1500)), (40000, 6, (17, 20000, 39999))])
+def test_spgemm_squaring_matches_scipy(sx, n, seed, dense):
+    """T~ = 2T + T T (Eq. 4.15), including rows wide enough for the global-scratch class."""
+    T = _ragged(n, seed, dense_rows=dense, empty_rows=[1])
+    tt = torch_csr(_csr(T))
+    (rp, ci, v), prod = sx.spgemm(tt, tt, tt, div=1.0, beta=2.0)
+    G = to_scipy(rp, ci, v, n)
+    R = O.square_raw(T)
+    _assert_product_parity(G, R)
+
+
+def _assert_product_parity(G, R):
+    G.sort_indices()
+    # every stored entry of the oracle is stored by the GPU; extra GPU entries are exact zeros
+    Gp = sp.csr_matrix((np.ones(G.nnz), G.indices, G.indptr), shape=G.shape)
+    Rp = sp.csr_matrix((np.ones(R.nnz), R.indices, R.indptr), shape=R.shape)
+    assert (Rp - Rp.multiply(Gp)).nnz == 0
+    extra = (Gp - Gp.multiply(Rp)).tocoo()
+    if extra.nnz:
+        assert np.all(np.asarray(G[extra.row, extra.col]).ravel() == 0.0)
+    D = (G - R)
+    scale = np.abs(R).max() if R.nnz else 1.0
+    assert (np.abs(D.data).max() if D.nnz else 0.0) <= 1e-13 * max(scale, 1e-300)
+    # rows are sorted with unique columns
+    for i in range(0, G.shape[0], max(1, G.shape[0] // 50)):
+        c = G.indices[G.indptr[i]:G.indptr[i + 1]]
+        assert np.all(np.diff(c) > 0)
+
+
+# ------------------------------------------------------------------ Algorithm 4.1
+
+@pytest.mark.parametrize("seed", range(4))
+def test_filter_matches_oracle(sx, seed):
+    rng = np.random.default_rng(seed)
+    n = [50, 400, 3000, 20000][seed]
+    A = sp.random(n, n, density=min(1.0, 30.0 / n), random_state=np.random.RandomState(seed), format="csr")
+    A.data = rng.standard_normal(A.nnz) * np.exp(rng.uniform(-45, 0, A.nnz))
+    eps_g = float(np.exp(rng.uniform(-35, -15)))
+    (rp, ci, v), t, iters, b = sx.filter_csr(torch_csr(_csr(A)), eps_g, 0.1)
+    t_o, it_o, b_o = O.alg41_threshold(A.data, eps_g, 0.1)
+    assert iters == it_o
+    assert t == pytest.approx(t_o, rel=1e-12)
+    assert b == pytest.approx(b_o, rel=1e-12)
+    G = to_scipy(rp, ci, v, n)
+    keep = np.abs(A.data) > t_o
+    near = np.abs(np.abs(A.data) - t_o) <= 1e-12 * t_o
+    Rk = A.copy(); Rk.data = np.where(keep, Rk.data, 0.0); Rk.eliminate_zeros()
+    diff = (G - Rk).tocsr()
+    assert diff.nnz == 0 or near.any()
+
+
+def test_filter_hand_trace(sx):
+    """Algorithm 4.1 on 1,2,3,4 with eps_g=3: two passes, t = 9/sqrt(14), keeps {3, 4}."""
+    A = sp.csr_matrix(np.array([[1.0, -2.0], [3.0, 4.0]]))
+    (rp, ci, v), t, iters, b = sx.filter_csr(torch_csr(_csr(A)), 3.0, 0.1)
+    assert iters == 2 and t == pytest.approx(9 / math.sqrt(14))
+    assert to_scipy(rp, ci, v, 2).toarray().tolist() == [[0.0, 0.0], [3.0, 4.0]]
+
+
+# ------------------------------------------------------------------ the whole method
+
+def _run_both(sx, H: CSR, tau, eps, **opts):
+    (rp, ci, v), st = sx.expm(torch_csr(H), tau, eps, **opts)
+    G = to_scipy(rp, ci, v, H.n)
+    kw = {}
+    if opts.get("square_scale", 1) == 0:
+        kw["square_scale"] = "abs"
+    E, so = O.expm(H.to_scipy(), tau, eps, **kw)
+    return G, st, E, so
+
+
+def _t_drop(st, so):
+    ts = [r["t"] for r in st["steps"]] + [s.t for s in so.steps] + [t.t for t in so.taylor]
+    return max(ts) if ts else 0.0
+
+
+def _check_method(sx, H, tau, eps, **opts):
+    G, st, E, so = _run_both(sx, H, tau, eps, **opts)
+    assert (st["M"], st["N"]) == (so.M, so.N)
+    assert bool(st["normal"]) == bool(so.normal)
+    assert st["norm_H"] == pytest.approx(so.normH, rel=1e-13)
+    if so.M:
+        assert st["a"] == pytest.approx(so.a, rel=1e-14)
+        assert st["r0"] == pytest.approx(so.r0, rel=1e-12)
+    res = expm_parity(G, E, _t_drop(st, so))
+    return res, st, so
+
+
+@pytest.mark.parametrize("name", ["lap2d_m32"])
+def test_expm_config_small_grid(sx, name):
+    c = get_config(name)
+    res, st, so = _check_method(sx, c.build(), c.tau, c.eps)
+    # the per-step record: same number of squarings, kept counts within the flip allowance
+    sq = [r for r in st["steps"] if r["phase"] == 1]
+    assert len(sq) == so.N
+    for r, s in zip(sq, so.steps):
+        assert r["nnz"] == pytest.approx(s.nnz, rel=2e-3)
+        assert r["eps_g"] == pytest.approx(s.eps_g, rel=1e-10)
+
+
+def test_expm_paper_toeplitz(sx):
+    H = toeplitz_trid(10_000, 1.0, -2.0, 1.0)
+    res, st, so = _check_method(sx, H, 1.0, 1e-16)
+    assert (st["M"], st["N"]) == (20, 8)
+
+
+def test_expm_heat_toeplitz(sx):
+    n = 10_000
+    H = toeplitz_trid(n, -1.0 / (n + 1), 2.0 / (n + 1), -1.0 / (n + 1))
+    _check_method(sx, H, 1.0, 1e-16)
+
+
+def test_expm_3d_grid_and_nonnormal_variant(sx):
+    L = dirichlet_laplacian(12, 3)
+    tau = 2.1125 / 13 ** 2
+    _check_method(sx, L, tau, 1e-12)
+    DL, _ = diag_scale(L, seed=1)
+    res, st, so = _check_method(sx, DL, tau, 1e-12)
+    assert not st["normal"]
+
+
+def test_expm_absolute_threshold_option(sx):
+    c = get_config("lap2d_m32")
+    _check_method(sx, c.build(), c.tau, c.eps, square_scale=0)
+
+
+def test_expm_random_graph(sx):
+    A = rgg_adjacency(3000, seed=7)
+    _check_method(sx, A, 0.5, 1e-12)
+
+
+@pytest.mark.parametrize("k", range(5))
+def test_expm_paper_table1(sx, k):
+    H = CSR.from_dense(paper_table1_matrices()[k])
+    _check_method(sx, H, 1.0, 1e-16)
+
+
+def test_expm_edge_cases(sx):
+    # n = 1 scalar exponential
+    H = CSR.from_dense([[-3.5]])
+    res, st, so = _check_method(sx, H, 0.7, 1e-14)
+    # zero matrix (explicitly stored zeros) -> identity
+    Z = CSR(3, np.array([0, 1, 1, 2], dtype=np.int64), np.array([1, 2], dtype=np.int32), np.zeros(2))
+    (rp, ci, v), st = sx.expm(torch_csr(Z), 1.0, 1e-12)
+    assert (st["M"], st["N"]) == (0, 0)
+    assert np.array_equal(to_scipy(rp, ci, v, 3).toarray(), np.eye(3))
+    # empty rows and a ragged random matrix
+    R = random_csr(700, 0.004, seed=9, scale=3.0)
+    _check_method(sx, R, 1.0, 1e-12)
+
+
+def test_expm_rejects_invalid_input(sx):
+    bad = CSR(2, np.array([0, 2, 3], dtype=np.int64), np.array([1, 0, 1], dtype=np.int32), np.ones(3))
+    with pytest.raises(sx.SexpmError) as ei:
+        sx.expm(torch_csr(bad), 1.0, 1e-12)
+    assert ei.value.code == -1
+    nanm = CSR(1, np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([np.nan]))
+    with pytest.raises(sx.SexpmError):
+        sx.expm(torch_csr(nanm), 1.0, 1e-12)
+    with pytest.raises(sx.SexpmError):
+        sx.expm(torch_csr(CSR.from_dense([[1.0]])), 1.0, 0.0)
