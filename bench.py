@@ -171,7 +171,7 @@ def run_ours(args):
     from paper_2110_04493_gb300 import sexpm
     from workloads import get_config
 
-    c = get_config(args.workload)
+    c = get_config(args.workload, args.scale_m)
     H = c.build()
     dev = (torch.from_numpy(H.row_ptr).cuda(), torch.from_numpy(H.col).cuda(), torch.from_numpy(H.val).cuda(), H.n)
     plan = sexpm.Plan(dev, c.eps)
@@ -277,7 +277,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "expm/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": c.desc, "n": H.n, "nnz_H": H.nnz,
+            "config": {"workload": c.name, "desc": c.desc, "n": H.n, "nnz_H": H.nnz,
                        "M": st["M"], "N": st["N"], "nnz_expm": st["nnz_out"],
                        "l2": "inputs larger than L2 (every squaring streams T^_i of > 129 MB)",
                        "parallelism": f"replicas x{ws}"},
@@ -294,7 +294,15 @@ def run_ours(args):
             "squaring_gflops_useful": (2.0 * sum(r["products"] for r in st["steps"] if r["phase"] == 1)) /
                                       (sq_step_ms * 1e-3) / 1e9 if sq_step_ms else None,
             "squaring_numeric_gflops": sq_flops / (sq_ms * 1e-3) / 1e9 if sq_ms else None,
-            "products": products, "peak_hbm_bytes": st["peak_bytes"],
+            "products": products, "products_done": sum(r["products_done"] for r in st["steps"]),
+            "symmetric_products": bool(st["symmetric"]), "peak_hbm_bytes": st["peak_bytes"],
+            "per_step": [{"phase": "taylor" if r["phase"] == 0 else "square", "i": r["i"], "products": r["products"],
+                          "products_done": r["products_done"],
+                          "nnz_raw": r["nnz_raw"], "nnz": r["nnz"], "t": r["t"], "iters": r["iters"],
+                          "ms": round(r["ms"], 3), "ms_numeric": round(r["ms_numeric"], 3),
+                          "ms_symbolic": round(r["ms_symbolic"], 3), "ms_filter": round(r["ms_filter"], 3),
+                          "numeric_gflops": round(r["flops"] / (r["ms_numeric"] * 1e6), 1) if r["ms_numeric"] else None}
+                         for r in st["steps"]] if args.per_step else None,
             "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -310,8 +318,11 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lap2d_m1500")
+    ap.add_argument("--scale-m", type=int, default=0,
+                    help="run the grid workload on an m-sided grid with the same tau/h^2 (profiling sizes)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--per-step", action="store_true", help="add the per-step records to the JSON line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-m", type=int, default=80,
                     help="grid side of the oracle's sample of the workload (same tau/h^2 and eps)")

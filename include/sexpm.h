@@ -68,6 +68,11 @@ typedef struct {
   int32_t max_filter_iters; /* Algorithm 4.1 iteration cap; default 100 */
   int32_t n_extra;          /* N_max = N_0 + n_extra in Eq. (4.20); default 50 */
   int32_t max_taylor;       /* cap on M (SEXPM_ENOPARAM above it); default 1000 */
+  int32_t symmetric;        /* 1 (default): when H == H^T exactly, T^_0 is symmetrised
+                               ((T^_0 + T^_0^T)/2; its asymmetry is at the level of the Taylor
+                               filter) and every squaring T~_i = 2T + T T, symmetric by
+                               construction, forms only the entries at columns >= row and
+                               mirrors the rest (halves the FP64 work); 0: form every entry */
 } sexpm_options;
 
 typedef struct sexpm_plan sexpm_plan_t;
@@ -85,12 +90,13 @@ typedef struct {
   double norm_F;      /* ||I + T~_i||_F (squaring steps; 0 for Taylor terms) */
   int64_t nnz_raw;    /* stored entries before filtering */
   int64_t nnz;        /* stored entries after filtering */
-  int64_t products;   /* scalar multiply-adds of the sparse product */
+  int64_t products;   /* scalar multiply-adds of the sparse product (all entries) */
+  int64_t products_done; /* multiply-adds actually formed (fewer in the symmetric mode) */
   double ms;          /* device time of the step (CUDA events) */
   double ms_symbolic; /* sparse product: row analysis, binning and symbolic pass */
   double ms_numeric;  /* sparse product: numeric pass (fused /i or + 2T) */
   double ms_filter;   /* Algorithm 4.1 passes, row-pointer scan and compaction */
-  double flops;       /* FP64 operations of the numeric pass: 2 products + the fused term */
+  double flops;       /* FP64 operations of the numeric pass: 2 products_done + the fused term */
   double bytes_filter;/* algorithmic bytes moved by the filter passes, scan and compaction */
 } sexpm_step_stats;
 
@@ -100,6 +106,8 @@ typedef struct {
   int32_t M, N;       /* Eq. (4.20) */
   int32_t normal;     /* 1 if H was treated as normal */
   int32_t n_steps;    /* entries filled in steps[] (<= max) */
+  int32_t symmetric;  /* 1 if the symmetric (upper-triangle) products were used */
+  int32_t pad_;
   double a;           /* filter parameter: 1/(N+1) (normal) or 1/||H||_F */
   double r0;          /* Eq. (4.5) at x = ||H 2^-N||_F */
   double eps_g0;      /* a r_0 / (M e^{2 ||H_0||_F}), the Taylor-phase bound */

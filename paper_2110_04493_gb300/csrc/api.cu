@@ -217,6 +217,7 @@ struct sexpm_plan {
   double eps = 0.0;
   CsrOwned H;
   int normal = 1;
+  bool symmetric = false;  // H == H^T exactly
   HostScalars hs;
 };
 
@@ -266,6 +267,7 @@ int sexpm_options_default(sexpm_options* opt) {
   opt->max_filter_iters = 100;
   opt->n_extra = 50;
   opt->max_taylor = 1000;
+  opt->symmetric = 1;
   return SEXPM_OK;
 }
 
@@ -274,6 +276,7 @@ static void check_options(const sexpm_options& o) {
   if (o.square_scale != 0 && o.square_scale != 1) fail(SEXPM_EINVAL, "square_scale must be 0 or 1");
   if (o.normal_override < -1 || o.normal_override > 1) fail(SEXPM_EINVAL, "normal_override must be -1, 0 or 1");
   if (o.max_filter_iters < 1 || o.n_extra < 0 || o.max_taylor < 1) fail(SEXPM_EINVAL, "bad iteration limits");
+  if (o.symmetric != 0 && o.symmetric != 1) fail(SEXPM_EINVAL, "symmetric must be 0 or 1");
 }
 
 int sexpm_plan(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_options* opt, void* stream,
@@ -291,13 +294,14 @@ int sexpm_plan(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_optio
     p->s = static_cast<cudaStream_t>(stream);
     p->eps = eps;
     upload(*H, p->s, p->H, p->hs);
+    CsrOwned Ht;
+    transpose(p->H.view(), p->s, Ht, p->hs);
+    p->symmetric = csr_equal(p->H.view(), Ht.view(), 1.0, p->s, p->hs);
     if (p->opt.normal_override >= 0) {
       p->normal = p->opt.normal_override;
     } else {
       // Algorithm 4.2 step 2: normality.  Exact symmetry / skew-symmetry first.
-      CsrOwned Ht;
-      transpose(p->H.view(), p->s, Ht, p->hs);
-      if (csr_equal(p->H.view(), Ht.view(), 1.0, p->s, p->hs) || csr_equal(p->H.view(), Ht.view(), -1.0, p->s, p->hs)) {
+      if (p->symmetric || csr_equal(p->H.view(), Ht.view(), -1.0, p->s, p->hs)) {
         p->normal = 1;
       } else {
         CsrOwned P, Q, C;
@@ -355,6 +359,8 @@ int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
     st.N = N;
     const bool normal = (p->normal != 0) || normH == 0.0;
     st.normal = normal ? 1 : 0;
+    const bool sym = p->symmetric && o.symmetric;
+    st.symmetric = sym ? 1 : 0;
     if (M == 0) {
       // ||tau H|| = 0: e^0 = I
       CsrOwned Z;
@@ -394,7 +400,8 @@ int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
       Timer ts(s);
       CsrOwned St;
       SpgemmTimes tm;
-      const int64_t prod = spgemm(Sv, H0, none, (double)i, 0.0, s, St, nullptr, hs, &tm);
+      int64_t done = 0;
+      const int64_t prod = spgemm(Sv, H0, none, (double)i, 0.0, s, St, nullptr, hs, &tm, false, &done);
       CsrOwned Sn;
       FilterOut fo = filter_alg41(St.view(), eps_g0, o.e_r, o.max_filter_iters, s, Sn, hs);
       sexpm_step_stats rec;
@@ -411,7 +418,8 @@ int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
       rec.ms_symbolic = tm.ms_symbolic;
       rec.ms_numeric = tm.ms_numeric;
       rec.ms_filter = fo.ms;
-      rec.flops = 2.0 * (double)prod + (double)St.nnz;
+      rec.products_done = done;
+      rec.flops = 2.0 * (double)done + (double)St.nnz;
       rec.bytes_filter = fo.bytes;
       if (Sn.nnz == 0) {
         rec.ms = ts.ms();
@@ -427,6 +435,15 @@ int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
       res->steps.push_back(rec);
     }
     S.rp.free(); S.ci.free(); S.v.free();
+    if (sym) {
+      // For symmetric H the exact T_0 is symmetric, but a filtered term S^_i no longer commutes
+      // with H_0, so S^_{i-1} H_0 (and T^_0) can lose symmetry at the level of the dropped
+      // entries.  T^_0 <- (T^_0 + T^_0^T)/2 restores it; from then on every T~_i = 2T + T T is
+      // symmetric and the squarings form only the entries at columns >= row.
+      CsrOwned Ts;
+      symmetric_part(T.view(), s, Ts, hs);
+      T = std::move(Ts);
+    }
     st.ms_taylor = t_tay.ms();
     // step 4: N filtered squarings
     Timer t_sq(s);
@@ -436,8 +453,9 @@ int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
       const double ri = std::ldexp(r0, i);
       CsrOwned Tt;
       SpgemmTimes tm;
-      const int64_t prod = spgemm(T.view(), T.view(), T.view(), 1.0, 2.0, s, Tt, &rs, hs, &tm);
-      const double flops = 2.0 * (double)prod + 2.0 * (double)T.nnz;
+      int64_t done = 0;
+      const int64_t prod = spgemm(T.view(), T.view(), T.view(), 1.0, 2.0, s, Tt, &rs, hs, &tm, sym, &done);
+      const double flops = 2.0 * (double)done + 2.0 * (double)T.nnz;
       double normF = 1.0;
       if (o.square_scale) {
         const double sq = reduce_sum(rs.sq.p, n, s, hs);
@@ -461,6 +479,7 @@ int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
       rec.nnz_raw = Tt.nnz;
       rec.nnz = Tn.nnz;
       rec.products = prod;
+      rec.products_done = done;
       rec.ms_symbolic = tm.ms_symbolic;
       rec.ms_numeric = tm.ms_numeric;
       rec.ms_filter = fo.ms;

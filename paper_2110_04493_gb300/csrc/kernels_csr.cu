@@ -325,6 +325,73 @@ __global__ void k_sort_rows(int64_t n, const int64_t* rp, int32_t* ci, double* v
   }
 }
 
+// ---- symmetric part: (A + A^T)/2 on the pattern of A; entries whose mirror is absent are flagged
+__device__ __forceinline__ int64_t lb_col(const int32_t* ci, int64_t lo, int64_t hi, int c) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (ci[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_sym_gather(CsrD A, double* out_v, uint8_t* lone, unsigned long long* n_lone) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
+    const int64_t p0 = A.rp[i], p1 = A.rp[i + 1];
+    for (int64_t p = p0 + lane_id(); p < p1; p += 32) {
+      const int j = A.ci[p];
+      const double a = A.v[p];
+      if (j == (int)i) {
+        out_v[p] = a;
+        lone[p] = 0;
+        continue;
+      }
+      const int64_t q0 = A.rp[j], q1 = A.rp[j + 1];
+      const int64_t q = lb_col(A.ci, q0, q1, (int)i);
+      if (q < q1 && A.ci[q] == (int)i) {
+        out_v[p] = 0.5 * (a + A.v[q]);
+        lone[p] = 0;
+      } else {
+        out_v[p] = 0.5 * a;
+        lone[p] = 1;
+        atomicAdd(n_lone, 1ull);
+      }
+    }
+  }
+}
+
+// Per-row count and compaction of the flagged entries (warp per row).
+__global__ void k_flag_count(CsrD A, const uint8_t* flag, int32_t* cnt) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
+    int c = 0;
+    for (int64_t p = A.rp[i] + lane_id(); p < A.rp[i + 1]; p += 32) c += flag[p];
+    c = warp_sum(c);
+    if (lane_id() == 0) cnt[i] = c;
+  }
+}
+
+__global__ void k_flag_compact(CsrD A, const double* vals, const uint8_t* flag, const int64_t* rp_out, int32_t* ci_out,
+                               double* v_out) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const unsigned lt = (1u << lane_id()) - 1u;
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
+    const int64_t q0 = A.rp[i], q1 = A.rp[i + 1];
+    int64_t o = rp_out[i];
+    for (int64_t qb = q0; qb < q1; qb += 32) {
+      const int64_t q = qb + lane_id();
+      const bool keep = q < q1 && flag[q];
+      const unsigned m = __ballot_sync(FULL, keep);
+      if (keep) {
+        const int64_t d = o + __popc(m & lt);
+        ci_out[d] = A.ci[q];
+        v_out[d] = vals[q];
+      }
+      o += __popc(m);
+    }
+  }
+}
+
 // ---- equality (B == sign * A, same pattern) and validation; flag[0] set on mismatch / invalid
 __global__ void k_equal(CsrD A, CsrD B, double sign, int* flag) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < A.nnz; q += (int64_t)gridDim.x * blockDim.x)
@@ -486,6 +553,50 @@ void transpose(const CsrD& A, cudaStream_t s, CsrOwned& T, HostScalars& hs) {
     count_launches(2);
   }
   SX_CUDA(cudaGetLastError());
+}
+
+void symmetric_part(const CsrD& A, cudaStream_t s, CsrOwned& S, HostScalars& hs) {
+  const int64_t n = A.n;
+  S.n = n;
+  S.nnz = A.nnz;
+  S.rp.reset(n + 1, s);
+  S.ci.reset(A.nnz, s);
+  S.v.reset(A.nnz, s);
+  if (n == 0) {
+    SX_CUDA(cudaMemsetAsync(S.rp.p, 0, sizeof(int64_t), s));
+    return;
+  }
+  SX_CUDA(cudaMemcpyAsync(S.rp.p, A.rp, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  if (A.nnz) SX_CUDA(cudaMemcpyAsync(S.ci.p, A.ci, A.nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  DevBuf<uint8_t> lone(A.nnz ? A.nnz : 1, s);
+  DevBuf<unsigned long long> cntr(1, s);
+  SX_CUDA(cudaMemsetAsync(cntr.p, 0, sizeof(unsigned long long), s));
+  const int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)sm_count() * 64);
+  k_sym_gather<<<blocks, 256, 0, s>>>(A, S.v.p, lone.p, cntr.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+  SX_CUDA(cudaMemcpyAsync(hs.i, cntr.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  SX_CUDA(cudaStreamSynchronize(s));
+  unsigned long long nl;
+  std::memcpy(&nl, hs.i, sizeof(nl));
+  if (nl == 0) return;
+  // entries whose mirror is absent: U (halved values) ; S <- S_avg + U^T
+  CsrOwned U, Ut, R;
+  U.n = n;
+  U.rp.reset(n + 1, s);
+  DevBuf<int32_t> cnt(n, s);
+  k_flag_count<<<blocks, 256, 0, s>>>(A, lone.p, cnt.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+  U.nnz = scan_counts(cnt.p, n, U.rp.p, s, hs);
+  U.ci.reset(U.nnz, s);
+  U.v.reset(U.nnz, s);
+  k_flag_compact<<<blocks, 256, 0, s>>>(A, S.v.p, lone.p, U.rp.p, U.ci.p, U.v.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+  transpose(U.view(), s, Ut, hs);
+  add(S.view(), Ut.view(), 1.0, s, R, hs);
+  S = std::move(R);
 }
 
 bool csr_equal(const CsrD& A, const CsrD& B, double sign, cudaStream_t s, HostScalars& hs) {

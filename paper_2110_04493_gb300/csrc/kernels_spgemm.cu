@@ -3,14 +3,23 @@
 // used for the Taylor terms S~_i = S^_{i-1} H_0 / i (Eq. 4.10) and the squaring
 // steps T~_i = 2 T^_{i-1} + T^_{i-1}^2 (Eq. 4.15).
 //
-// Row-wise (Gustavson) product, one thread block per output row.  The output
-// pattern of a row is held as a bitmap over the row's column span
-// [base, hi] (base rounded down to a multiple of 32).  A symbolic pass builds
-// the bitmap and counts its bits; the numeric pass rebuilds it, turns it into
-// per-word prefix counts, and uses rank(c) = pre[c/32] + popc(bm[c/32] & below(c))
-// as a perfect hash into a dense accumulator of exactly nnz(row) doubles.  The
-// accumulator is therefore already in sorted column order and is written out
-// with coalesced stores; no hash probing and no sort are needed.
+// Row-wise (Gustavson) product, one thread block per output row.
+//
+// Pattern.  The output pattern of row i is a bitmap over the row's column span
+// [base_i, hi_i] (base_i a multiple of 32).  B and D are first compressed to
+// "word patterns": for every row, the distinct 32-column words it touches and
+// the bit mask inside each word.  The row bitmap is then the OR of the word
+// patterns of the rows B_k, k in A_i (plus D_i), which costs one shared-memory
+// atomicOr per (k, word) instead of one per scalar product.  The symbolic pass
+// counts the bits; the numeric pass rebuilds the bitmap the same cheap way.
+//
+// Values.  rank(c) = pre[c/32] + popc(bm[c/32] & below(c)) maps a column to
+// its position in the sorted output row, so the accumulator is a dense array
+// of exactly nnz(row) doubles already in column order.  The accumulator is
+// owner-computes: the row's positions are split into equal contiguous ranges,
+// one per warp; each warp visits every k of A_i, takes the part of B_k whose
+// columns fall inside its range (found by binary search), and updates its own
+// positions with a plain FMA (no atomics, one FP64 operation per product).
 //
 // Rows are binned by the shared memory they need (bitmap, prefix counts and
 // accumulator); the widest rows use a per-block global-memory scratch slice.
@@ -19,6 +28,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <string>
 
 #include "sexpm_internal.cuh"
 
@@ -26,14 +36,36 @@ namespace sexpm {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kClasses = 5;
+constexpr int kClasses = 6;
 // Shared-memory budget and block size of each row class; the last class uses global scratch.
-constexpr int kClassBytes[kClasses] = {4 << 10, 16 << 10, 64 << 10, 200 << 10, INT_MAX};
-constexpr int kClassThreads[kClasses] = {64, 128, 256, 512, 512};
+// With at most 64 registers per thread, 256-thread blocks of up to 56 KB run four per SM.
+constexpr int kClassBytes[kClasses] = {8 << 10, 24 << 10, 56 << 10, 112 << 10, 220 << 10, INT_MAX};
+constexpr int kClassThreads[kClasses] = {64, 128, 256, 256, 512, 512};
 
 __host__ __device__ constexpr int class_limit(int c) {
-  return c == 0 ? (4 << 10) : c == 1 ? (16 << 10) : c == 2 ? (64 << 10) : c == 3 ? (200 << 10) : INT_MAX;
+  return c == 0 ? (8 << 10) : c == 1 ? (24 << 10) : c == 2 ? (56 << 10) : c == 3 ? (112 << 10)
+       : c == 4 ? (220 << 10) : INT_MAX;
 }
+
+// Shared bytes the numeric pass needs for a row with W bitmap words and cnt outputs: the
+// accumulator (8 cnt bytes, which first holds the per-word product counts, 4 W bytes),
+// the bitmap and the position prefix (4 W bytes each).
+__host__ __device__ __forceinline__ long long acc_region(long long W, long long cnt) {
+  const long long a = 8 * cnt, w = 4 * W;
+  return ((a > w ? a : w) + 15) & ~15ll;
+}
+// Position prefixes are stored as 16-bit counts when the row has fewer than 65536 entries.
+__host__ __device__ __forceinline__ bool small_prefix(long long cnt) { return cnt < 65536; }
+__host__ __device__ __forceinline__ long long numeric_need(long long W, long long cnt) {
+  return acc_region(W, cnt) + 4 * W + (((small_prefix(cnt) ? 2 * W : 4 * W) + 15) & ~15ll);
+}
+
+// Word pattern of a CSR matrix: row r touches words wi[rp[r] .. rp[r+1]) with masks wb[...].
+struct WPat {
+  const int64_t* rp = nullptr;
+  const int32_t* wi = nullptr;
+  const uint32_t* wb = nullptr;
+};
 
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
@@ -57,24 +89,6 @@ __device__ T block_sum(T v, T* red) {
   return t;
 }
 
-// Sets the bits of column offsets c (relative to the row's base) held by the active lanes.
-// Active lanes form a prefix of the warp and their offsets increase with the lane index,
-// so lanes hitting the same 32-bit word are contiguous: OR them together with a segmented
-// down-sweep and let the first lane of each segment issue one atomicOr.
-__device__ __forceinline__ void warp_set_bits(uint32_t* bm, int c, bool act) {
-  const int lane = lane_id();
-  int w = act ? (c >> 5) : -1;
-  uint32_t bits = act ? (1u << (c & 31)) : 0u;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    uint32_t ob = __shfl_down_sync(FULL, bits, off);
-    int ow = __shfl_down_sync(FULL, w, off);
-    if (lane + off < 32 && ow == w) bits |= ob;
-  }
-  int pw = __shfl_up_sync(FULL, w, 1);
-  if (act && (lane == 0 || pw != w)) atomicOr(&bm[w], bits);
-}
-
 // Position of the r-th (0-based) set bit of m; m has more than r set bits.
 __device__ __forceinline__ int select_bit(uint32_t m, int r) {
   int pos = 0;
@@ -91,6 +105,91 @@ __device__ __forceinline__ int select_bit(uint32_t m, int r) {
   return pos;
 }
 
+// Column (relative to the row base) of output position k: the largest word w with
+// pre[w] <= k, then the (k - pre[w])-th set bit of that word.
+template <typename PreT>
+__device__ __forceinline__ int column_at(const uint32_t* bm, const PreT* pre, int W, int k) {
+  int lo = 0, hi = W - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int)pre[mid] <= k) lo = mid; else hi = mid - 1;
+  }
+  return lo * 32 + select_bit(bm[lo], k - (int)pre[lo]);
+}
+
+template <typename PreT>
+__device__ __forceinline__ unsigned rank_of(const uint32_t* bm, const PreT* pre, int c) {
+  const int w = c >> 5;
+  return pre[w] + __popc(bm[w] & ((1u << (c & 31)) - 1u));
+}
+
+__device__ __forceinline__ int64_t lower_bound_col(const int32_t* ci, int64_t lo, int64_t hi, int c) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (ci[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------- word patterns
+// Number of distinct words per row (one warp per row; rows are sorted).
+__global__ void k_wcount(CsrD X, int32_t* cnt) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < X.n; i += nw) {
+    const int64_t p0 = X.rp[i], p1 = X.rp[i + 1];
+    int c = 0;
+    int prev = -1;
+    for (int64_t q0 = p0; q0 < p1; q0 += 32) {
+      const int64_t q = q0 + lane_id();
+      const bool act = q < p1;
+      const int w = act ? (X.ci[q] >> 5) : -2;
+      int pw = __shfl_up_sync(FULL, w, 1);
+      if (lane_id() == 0) pw = prev;
+      c += __popc(__ballot_sync(FULL, act && w != pw));
+      prev = __shfl_sync(FULL, w, (int)(p1 - q0 - 1 < 31 ? p1 - q0 - 1 : 31));
+    }
+    if (lane_id() == 0) cnt[i] = c;
+  }
+}
+
+// Writes the word pattern: distinct words and the OR of their column bits.
+__global__ void k_wwrite(CsrD X, const int64_t* wrp, int32_t* wi, uint32_t* wb) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const unsigned lt = (1u << lane_id()) - 1u;
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < X.n; i += nw) {
+    const int64_t p0 = X.rp[i], p1 = X.rp[i + 1];
+    int64_t o = wrp[i];
+    int prev = -1;
+    for (int64_t q0 = p0; q0 < p1; q0 += 32) {
+      __syncwarp();
+      const int64_t q = q0 + lane_id();
+      const bool act = q < p1;
+      const int col = act ? X.ci[q] : 0;
+      const int w = act ? (col >> 5) : -2;
+      uint32_t bits = act ? (1u << (col & 31)) : 0u;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t ob = __shfl_down_sync(FULL, bits, off);
+        const int ow = __shfl_down_sync(FULL, w, off);
+        if (lane_id() + off < 32 && ow == w) bits |= ob;
+      }
+      int pw = __shfl_up_sync(FULL, w, 1);
+      if (lane_id() == 0) pw = prev;
+      const bool head = act && w != pw;
+      const unsigned hm = __ballot_sync(FULL, head);
+      if (head) {
+        const int64_t d = o + __popc(hm & lt);
+        wi[d] = w;
+        wb[d] = bits;
+      }
+      if (lane_id() == 0 && act && w == prev) wb[o - 1] |= bits;  // word continued from the previous chunk
+      o += __popc(hm);
+      prev = __shfl_sync(FULL, w, (int)(p1 - q0 - 1 < 31 ? p1 - q0 - 1 : 31));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- row analysis and binning
 // Per row: column span of the product row (A B plus the pattern of D) and its product count.
 // One warp per row.
 __global__ void k_analysis(CsrD A, CsrD B, CsrD D, int32_t* base, int32_t* words, int64_t* flops) {
@@ -135,8 +234,9 @@ __global__ void k_analysis(CsrD A, CsrD B, CsrD D, int32_t* base, int32_t* words
   }
 }
 
-// Assign each row to a class by its shared-memory need (bytes); append row ids per class.
-// mode 0: symbolic need 4 W; mode 1: numeric need 8 W + 8 cnt.
+// Assign each row to a class by its shared-memory need (bytes); append row ids per class and
+// record the largest need of each class (maxneed[class]).
+// mode 0: symbolic need 4 W; mode 1: numeric need 12 W + 8 cnt.
 __global__ void k_classify(int64_t n, const int32_t* words, const int64_t* rp_out, int mode,
                            int32_t* lists, int64_t list_stride, unsigned long long* counts,
                            unsigned long long* maxneed) {
@@ -153,53 +253,108 @@ __global__ void k_classify(int64_t n, const int32_t* words, const int64_t* rp_ou
     if (mode == 0) {
       need = 4 * W;
     } else {
-      need = 8 * W + 8 * (rp_out[i + 1] - rp_out[i]);
+      need = numeric_need(W, rp_out[i + 1] - rp_out[i]);
     }
     if (W > 0) {
       cls = 0;
       while (cls < kClasses - 1 && need > class_limit(cls)) ++cls;
       slot = atomicAdd(&cnt[cls], 1u);
-      if (cls == kClasses - 1) atomicMax(maxneed, (unsigned long long)need);
+      atomicMax(&maxneed[cls], (unsigned long long)need);
     }
   }
   __syncthreads();
-  if (threadIdx.x < kClasses) off[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&counts[threadIdx.x], (unsigned long long)cnt[threadIdx.x]) : 0ull;
+  if (threadIdx.x < kClasses)
+    off[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&counts[threadIdx.x], (unsigned long long)cnt[threadIdx.x]) : 0ull;
   __syncthreads();
   if (cls >= 0) lists[cls * list_stride + off[cls] + slot] = (int32_t)i;
 }
 
+// OR the word patterns of the rows B_k (k in A_i) and of D_i into the row bitmap bm
+// (word wlo of the row is bm[0]).  When work != nullptr, work[w] also receives the number of
+// scalar products that land in word w (the popcount of every B_k mask ORed into it).
+// Block-wide; the caller synchronises afterwards.
+// With upper set, only products at columns >= i are counted as work.
+__device__ __forceinline__ void build_row_bitmap(const CsrD& A, const WPat& WB, const WPat& WD, bool hasD, int64_t i,
+                                                 int wlo, uint32_t* bm, unsigned* work, bool upper) {
+  const int nwarps = blockDim.x >> 5;
+  const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
+  const int iw = (int)(i >> 5);
+  const uint32_t imask = ~((1u << (i & 31)) - 1u);
+  for (int64_t p = a0 + warp_id(); p < a1; p += nwarps) {
+    const int k = A.ci[p];
+    const int64_t e1 = WB.rp[k + 1];
+    for (int64_t e = WB.rp[k] + lane_id(); e < e1; e += 32) {
+      const int wa = WB.wi[e];
+      const int w = wa - wlo;
+      const uint32_t bits = WB.wb[e];
+      atomicOr(&bm[w], bits);
+      if (work) {
+        const uint32_t wbits = !upper || wa > iw ? bits : (wa == iw ? (bits & imask) : 0u);
+        if (wbits) atomicAdd(&work[w], (unsigned)__popc(wbits));
+      }
+    }
+  }
+  if (hasD) {
+    const int64_t e1 = WD.rp[i + 1];
+    for (int64_t e = WD.rp[i] + threadIdx.x; e < e1; e += blockDim.x) atomicOr(&bm[WD.wi[e] - wlo], WD.wb[e]);
+  }
+}
+
+// In-place exclusive scan of x[0..W) by the whole block; returns the total to every thread.
+// Each thread scans a contiguous chunk; `red` is a 32-entry shared scratch.
+__device__ unsigned block_exclusive_scan(unsigned* x, int W, unsigned* red) {
+  const int T = blockDim.x, nwarps = T >> 5, lane = lane_id();
+  const int ch = (W + T - 1) / T;
+  const int w0 = min(W, (int)threadIdx.x * ch), w1 = min(W, w0 + ch);
+  unsigned s = 0;
+  for (int w = w0; w < w1; ++w) s += x[w];
+  unsigned incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) red[warp_id()] = incl;
+  __syncthreads();
+  if (warp_id() == 0) {
+    const unsigned v = lane < nwarps ? red[lane] : 0u;
+    unsigned vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(FULL, vi, o);
+      if (lane >= o) vi += y;
+    }
+    if (lane < nwarps) red[lane] = vi - v;
+    if (lane == 31) red[31] = vi;  // block total (nwarps <= 16 < 32)
+  }
+  __syncthreads();
+  unsigned run = red[warp_id()] + incl - s;
+  for (int w = w0; w < w1; ++w) {
+    const unsigned v = x[w];
+    x[w] = run;
+    run += v;
+  }
+  const unsigned total = red[31];
+  __syncthreads();
+  return total;
+}
+
 // Symbolic pass: cnt[i] = number of distinct columns of row i of A B (+ pattern of D).
 template <bool GLOBAL>
-__global__ void k_symbolic(CsrD A, CsrD B, CsrD D, const int32_t* rows, int64_t nrows, const int32_t* base,
-                           const int32_t* words, int32_t* cnt, uint32_t* gscratch, int64_t gstride) {
+__global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const int32_t* rows, int64_t nrows,
+                           const int32_t* base, const int32_t* words, int32_t* cnt, uint32_t* gscratch,
+                           int64_t gstride) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int red[32];
   uint32_t* bm = GLOBAL ? gscratch + (int64_t)blockIdx.x * gstride : reinterpret_cast<uint32_t*>(smem);
-  const int nwarps = blockDim.x >> 5;
   for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int i = rows[r];
     const int W = words[i];
-    const int b = base[i];
+    const int wlo = base[i] >> 5;
     for (int w = threadIdx.x; w < W; w += blockDim.x) bm[w] = 0u;
     __syncthreads();
-    const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
-    for (int64_t p = a0 + warp_id(); p < a1; p += nwarps) {
-      const int k = A.ci[p];
-      const int64_t b0 = B.rp[k], b1 = B.rp[k + 1];
-      for (int64_t q0 = b0; q0 < b1; q0 += 32) {
-        const int64_t q = q0 + lane_id();
-        const bool act = q < b1;
-        warp_set_bits(bm, act ? B.ci[q] - b : 0, act);
-      }
-    }
-    if (D.n > 0 && warp_id() == 0) {
-      const int64_t d0 = D.rp[i], d1 = D.rp[i + 1];
-      for (int64_t q0 = d0; q0 < d1; q0 += 32) {
-        const int64_t q = q0 + lane_id();
-        const bool act = q < d1;
-        warp_set_bits(bm, act ? D.ci[q] - b : 0, act);
-      }
-    }
+    build_row_bitmap(A, WB, WD, hasD, i, wlo, bm, nullptr, false);
     __syncthreads();
     int c = 0;
     for (int w = threadIdx.x; w < W; w += blockDim.x) c += __popc(bm[w]);
@@ -209,18 +364,202 @@ __global__ void k_symbolic(CsrD A, CsrD B, CsrD D, const int32_t* rows, int64_t 
   }
 }
 
-// Numeric pass.  Shared layout per row: acc[cnt] doubles, bm[W] words, pre[W] prefix counts.
-template <bool GLOBAL>
-__global__ void k_numeric(CsrD A, CsrD B, CsrD D, double div, double beta, const int32_t* rows, int64_t nrows,
-                          const int32_t* base, const int32_t* words, const int64_t* rp_out, int32_t* ci_out,
-                          double* v_out, double* row_sq, double* row_diag, unsigned char* gscratch,
-                          int64_t gstride) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int ired[32];
-  __shared__ double dred[32];
-  unsigned char* mem = GLOBAL ? gscratch + (int64_t)blockIdx.x * gstride : smem;
+// Exclusive prefix of popc(bm[w]) into pre[0..W) (type PreT) by the whole block.
+template <typename PreT>
+__device__ void block_popc_prefix(const uint32_t* bm, PreT* pre, int W, unsigned* red) {
+  const int T = blockDim.x, nwarps = T >> 5, lane = lane_id();
+  const int ch = (W + T - 1) / T;
+  const int w0 = min(W, (int)threadIdx.x * ch), w1 = min(W, w0 + ch);
+  unsigned s = 0;
+  for (int w = w0; w < w1; ++w) s += __popc(bm[w]);
+  unsigned incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) red[warp_id()] = incl;
+  __syncthreads();
+  if (warp_id() == 0) {
+    const unsigned v = lane < nwarps ? red[lane] : 0u;
+    unsigned vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(FULL, vi, o);
+      if (lane >= o) vi += y;
+    }
+    if (lane < nwarps) red[lane] = vi - v;
+  }
+  __syncthreads();
+  unsigned run = red[warp_id()] + incl - s;
+  for (int w = w0; w < w1; ++w) {
+    pre[w] = (PreT)run;
+    run += __popc(bm[w]);
+  }
+  __syncthreads();
+}
+
+// Numeric pass, one row: prefixes, owner-computes accumulation, fused scaling and beta D,
+// and the ordered write.  acc/wk share the accumulator region; bm holds the row bitmap.
+template <typename PreT>
+__device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, bool upper, int i,
+                            int W, int b, int64_t o0, int cnt, double* acc, unsigned* wk, const uint32_t* bm,
+                            PreT* pre, int32_t* ci_out, double* v_out, double* row_sq, double* row_diag,
+                            unsigned* ured, double* dred, unsigned long long* work_total) {
   const int nwarps = blockDim.x >> 5;
   const int T = blockDim.x;
+  const int lane = lane_id();
+  const bool hasD = D.n > 0;
+  // 2. exclusive prefixes: output positions (pre) and products (wk) per word
+  block_popc_prefix(bm, pre, W, ured);
+  const unsigned work = block_exclusive_scan(wk, W, ured);
+  if (threadIdx.x == 0) atomicAdd(work_total, (unsigned long long)work);
+  // 3. owner-computes accumulation.  Warp w owns the words [wa, wb) that hold the w-th
+  //    equal share of the row's products, i.e. the columns [b + 32 wa, b + 32 wb).
+  {
+    const unsigned t0 = (unsigned)(((unsigned long long)warp_id() * work) / nwarps);
+    const unsigned t1 = (unsigned)(((unsigned long long)(warp_id() + 1) * work) / nwarps);
+    // first word whose prefix is >= target (words before it end before the target)
+    int wa = 0, wb = 0;
+    {
+      int lo = 0, hi = W;
+      while (lo < hi) { const int mid = (lo + hi) >> 1; if (wk[mid] < t0) lo = mid + 1; else hi = mid; }
+      wa = lo;
+      lo = wa; hi = W;
+      while (lo < hi) { const int mid = (lo + hi) >> 1; if (wk[mid] < t1) lo = mid + 1; else hi = mid; }
+      wb = (warp_id() == nwarps - 1) ? W : lo;
+    }
+    __syncthreads();  // every warp has read wk: the region now becomes the accumulator
+    for (int k = threadIdx.x; k < cnt; k += T) acc[k] = 0.0;
+    __syncthreads();
+    if (wa < wb) {
+      const int c_lo = upper ? max(b + 32 * wa, i) : b + 32 * wa;
+      const int c_hi = b + 32 * wb - 1;
+      const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
+      for (int64_t kb = a0; kb < a1; kb += 32) {
+        const int64_t p = kb + lane;
+        int64_t s = 0, e = 0;
+        double a = 0.0;
+        if (p < a1) {
+          const int k = A.ci[p];
+          a = A.v[p];
+          const int64_t b0 = B.rp[k], b1 = B.rp[k + 1];
+          s = e = b0;
+          if (b1 > b0) {
+            const int f = B.ci[b0], l = B.ci[b1 - 1];
+            if (f <= c_hi && l >= c_lo) {
+              s = f >= c_lo ? b0 : lower_bound_col(B.ci, b0, b1, c_lo);
+              e = l <= c_hi ? b1 : lower_bound_col(B.ci, s, b1, c_hi + 1);
+            }
+          }
+        }
+        const int nb = (int)(a1 - kb < 32 ? a1 - kb : 32);
+        // software pipeline: the first four chunks of the next segment are loaded while the
+        // current segment is accumulated.  All entries of one segment belong to one row B_k,
+        // so their columns (and positions) are distinct within a round.
+        int64_t sj = __shfl_sync(FULL, s, 0), ej = __shfl_sync(FULL, e, 0);
+        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        {
+          const int64_t q = sj + lane;
+          if (q < ej) { c0 = __ldg(B.ci + q); v0 = __ldg(B.v + q); }
+          if (q + 32 < ej) { c1 = __ldg(B.ci + q + 32); v1 = __ldg(B.v + q + 32); }
+          if (q + 64 < ej) { c2 = __ldg(B.ci + q + 64); v2 = __ldg(B.v + q + 64); }
+          if (q + 96 < ej) { c3 = __ldg(B.ci + q + 96); v3 = __ldg(B.v + q + 96); }
+        }
+        for (int j = 0; j < nb; ++j) {
+          const double aj = __shfl_sync(FULL, a, j);
+          const int jn = j + 1 < nb ? j + 1 : j;
+          const int64_t sn = __shfl_sync(FULL, s, jn);
+          const int64_t en = j + 1 < nb ? __shfl_sync(FULL, e, jn) : sn;
+          int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+          double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+          {
+            const int64_t q = sn + lane;
+            if (q < en) { n0 = __ldg(B.ci + q); u0 = __ldg(B.v + q); }
+            if (q + 32 < en) { n1 = __ldg(B.ci + q + 32); u1 = __ldg(B.v + q + 32); }
+            if (q + 64 < en) { n2 = __ldg(B.ci + q + 64); u2 = __ldg(B.v + q + 64); }
+            if (q + 96 < en) { n3 = __ldg(B.ci + q + 96); u3 = __ldg(B.v + q + 96); }
+          }
+          const int64_t q = sj + lane;
+          if (q < ej) { const int pp = (int)rank_of(bm, pre, c0 - b); acc[pp] = fma(aj, v0, acc[pp]); }
+          if (q + 32 < ej) { const int pp = (int)rank_of(bm, pre, c1 - b); acc[pp] = fma(aj, v1, acc[pp]); }
+          if (q + 64 < ej) { const int pp = (int)rank_of(bm, pre, c2 - b); acc[pp] = fma(aj, v2, acc[pp]); }
+          if (q + 96 < ej) { const int pp = (int)rank_of(bm, pre, c3 - b); acc[pp] = fma(aj, v3, acc[pp]); }
+          // rest of a long segment
+          for (int64_t qq = sj + 128 + lane; qq < ej; qq += 128) {
+            const bool m1 = qq + 32 < ej, m2 = qq + 64 < ej, m3 = qq + 96 < ej;
+            const int d0 = __ldg(B.ci + qq);
+            const double x0 = __ldg(B.v + qq);
+            int d1 = 0, d2 = 0, d3 = 0;
+            double x1 = 0.0, x2 = 0.0, x3 = 0.0;
+            if (m1) { d1 = __ldg(B.ci + qq + 32); x1 = __ldg(B.v + qq + 32); }
+            if (m2) { d2 = __ldg(B.ci + qq + 64); x2 = __ldg(B.v + qq + 64); }
+            if (m3) { d3 = __ldg(B.ci + qq + 96); x3 = __ldg(B.v + qq + 96); }
+            { const int pp = (int)rank_of(bm, pre, d0 - b); acc[pp] = fma(aj, x0, acc[pp]); }
+            if (m1) { const int pp = (int)rank_of(bm, pre, d1 - b); acc[pp] = fma(aj, x1, acc[pp]); }
+            if (m2) { const int pp = (int)rank_of(bm, pre, d2 - b); acc[pp] = fma(aj, x2, acc[pp]); }
+            if (m3) { const int pp = (int)rank_of(bm, pre, d3 - b); acc[pp] = fma(aj, x3, acc[pp]); }
+          }
+          __syncwarp();
+          sj = sn; ej = en;
+          c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+          v0 = u0; v1 = u1; v2 = u2; v3 = u3;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // 4. scaling (Taylor /i) and the fused beta D term (squaring +2T), in that order
+  if (div != 1.0)
+    for (int k = threadIdx.x; k < cnt; k += T) acc[k] = acc[k] / div;
+  __syncthreads();
+  if (hasD) {
+    const int64_t d0 = D.rp[i], d1 = D.rp[i + 1];
+    for (int64_t q = d0 + threadIdx.x; q < d1; q += T) {
+      const int c = D.ci[q];
+      if (upper && c < i) continue;
+      const int pos = (int)rank_of(bm, pre, c - b);
+      acc[pos] += beta * D.v[q];
+    }
+  }
+  __syncthreads();
+  // 5. write the row in column order; per-row sum of squares and diagonal
+  //    (upper: values below the diagonal are filled afterwards from the mirror entries, and an
+  //    off-diagonal entry stands for itself and its mirror in the sum of squares)
+  double sq = 0.0;
+  for (int k = threadIdx.x; k < cnt; k += T) {
+    const int col = b + column_at(bm, pre, W, k);
+    ci_out[o0 + k] = col;
+    if (upper && col < i) continue;
+    const double v = acc[k];
+    v_out[o0 + k] = v;
+    sq += (upper && col != i) ? 2.0 * v * v : v * v;
+    if (row_diag && col == i) row_diag[i] = v;
+  }
+  if (row_sq) {
+    sq = block_sum(sq, dred);
+    if (threadIdx.x == 0) row_sq[i] = sq;
+  }
+  __syncthreads();
+}
+
+// Numeric pass.  Layout per row: an accumulator region (acc[cnt] doubles; before the
+// accumulation it holds wk[W], the prefix product counts), bm[W] words, pre[W] position
+// prefixes (16- or 32-bit).
+template <bool GLOBAL>
+__global__ void k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, double beta, bool upper,
+                          const int32_t* rows,
+                          int64_t nrows, const int32_t* base, const int32_t* words, const int64_t* rp_out,
+                          int32_t* ci_out, double* v_out, double* row_sq, double* row_diag, unsigned char* gscratch,
+                          int64_t gstride, unsigned long long* work_total) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned ured[32];
+  __shared__ double dred[32];
+  unsigned char* mem = GLOBAL ? gscratch + (int64_t)blockIdx.x * gstride : smem;
+  const int T = blockDim.x;
+  const bool hasD = D.n > 0;
   for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int i = rows[r];
     const int W = words[i];
@@ -228,112 +567,45 @@ __global__ void k_numeric(CsrD A, CsrD B, CsrD D, double div, double beta, const
     const int64_t o0 = rp_out[i];
     const int cnt = (int)(rp_out[i + 1] - o0);
     double* acc = reinterpret_cast<double*>(mem);
-    uint32_t* bm = reinterpret_cast<uint32_t*>(acc + cnt);
-    int* pre = reinterpret_cast<int*>(bm + W);
-    for (int w = threadIdx.x; w < W; w += T) bm[w] = 0u;
-    for (int k = threadIdx.x; k < cnt; k += T) acc[k] = 0.0;
+    unsigned* wk = reinterpret_cast<unsigned*>(mem);
+    uint32_t* bm = reinterpret_cast<uint32_t*>(mem + acc_region(W, cnt));
+    for (int w = threadIdx.x; w < W; w += T) {
+      bm[w] = 0u;
+      wk[w] = 0u;
+    }
     if (row_diag && threadIdx.x == 0) row_diag[i] = 0.0;
     __syncthreads();
-    // 1. pattern bitmap (as in the symbolic pass)
-    const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
-    for (int64_t p = a0 + warp_id(); p < a1; p += nwarps) {
-      const int k = A.ci[p];
-      const int64_t b0 = B.rp[k], b1 = B.rp[k + 1];
-      for (int64_t q0 = b0; q0 < b1; q0 += 32) {
-        const int64_t q = q0 + lane_id();
-        const bool act = q < b1;
-        warp_set_bits(bm, act ? B.ci[q] - b : 0, act);
-      }
-    }
-    if (D.n > 0 && warp_id() == 0) {
-      const int64_t d0 = D.rp[i], d1 = D.rp[i + 1];
-      for (int64_t q0 = d0; q0 < d1; q0 += 32) {
-        const int64_t q = q0 + lane_id();
-        const bool act = q < d1;
-        warp_set_bits(bm, act ? D.ci[q] - b : 0, act);
-      }
-    }
+    // 1. pattern bitmap and products per word, from the word patterns
+    build_row_bitmap(A, WB, WD, hasD, i, b >> 5, bm, wk, upper);
     __syncthreads();
-    // 2. exclusive prefix of the per-word popcounts: each thread scans a contiguous chunk
-    {
-      const int ch = (W + T - 1) / T;
-      const int w0 = min(W, threadIdx.x * ch), w1 = min(W, w0 + ch);
-      int s = 0;
-      for (int w = w0; w < w1; ++w) s += __popc(bm[w]);
-      // block exclusive scan of s
-      int incl = s;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(FULL, incl, o);
-        if (lane_id() >= o) incl += y;
-      }
-      if (lane_id() == 31) ired[warp_id()] = incl;
-      __syncthreads();
-      if (warp_id() == 0) {
-        int v = lane_id() < nwarps ? ired[lane_id()] : 0;
-        int vi = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          int y = __shfl_up_sync(FULL, vi, o);
-          if (lane_id() >= o) vi += y;
-        }
-        if (lane_id() < nwarps) ired[lane_id()] = vi - v;
-      }
-      __syncthreads();
-      int run = ired[warp_id()] + incl - s;
-      for (int w = w0; w < w1; ++w) {
-        pre[w] = run;
-        run += __popc(bm[w]);
+    if (small_prefix(cnt))
+      numeric_row(A, B, D, div, beta, upper, i, W, b, o0, cnt, acc, wk, bm,
+                  reinterpret_cast<unsigned short*>(bm + W), ci_out, v_out, row_sq, row_diag, ured, dred, work_total);
+    else
+      numeric_row(A, B, D, div, beta, upper, i, W, b, o0, cnt, acc, wk, bm, reinterpret_cast<unsigned*>(bm + W),
+                  ci_out, v_out, row_sq, row_diag, ured, dred, work_total);
+  }
+}
+
+// Fills the entries below the diagonal of a structurally symmetric product whose upper part
+// (columns >= row) was computed: C[i][j] = C[j][i] for j < i, found by binary search in row j.
+// One warp per row.  A partner that is absent (the pattern was not symmetric) counts a miss.
+__global__ void k_mirror(int64_t n, const int64_t* rp, const int32_t* ci, double* v, unsigned long long* misses) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < n; i += nw) {
+    const int64_t p0 = rp[i], p1 = rp[i + 1];
+    for (int64_t p = p0 + lane_id(); p < p1; p += 32) {
+      const int j = ci[p];
+      if (j >= i) break;
+      const int64_t q0 = rp[j], q1 = rp[j + 1];
+      const int64_t q = lower_bound_col(ci, q0, q1, (int)i);
+      if (q < q1 && ci[q] == (int)i) {
+        v[p] = v[q];
+      } else {
+        v[p] = 0.0;
+        atomicAdd(misses, 1ull);
       }
     }
-    __syncthreads();
-    // 3. accumulate the products a_ik b_kj at rank(j)
-    for (int64_t p = a0 + warp_id(); p < a1; p += nwarps) {
-      const int k = A.ci[p];
-      const double a = A.v[p];
-      const int64_t b0 = B.rp[k], b1 = B.rp[k + 1];
-      for (int64_t q = b0 + lane_id(); q < b1; q += 32) {
-        const int c = B.ci[q] - b;
-        const int w = c >> 5;
-        const int pos = pre[w] + __popc(bm[w] & ((1u << (c & 31)) - 1u));
-        atomicAdd(&acc[pos], a * B.v[q]);
-      }
-    }
-    __syncthreads();
-    // 4. scaling (Taylor /i) and the fused beta D term (squaring +2T), in that order
-    if (div != 1.0)
-      for (int k = threadIdx.x; k < cnt; k += T) acc[k] = acc[k] / div;
-    __syncthreads();
-    if (D.n > 0) {
-      const int64_t d0 = D.rp[i], d1 = D.rp[i + 1];
-      for (int64_t q = d0 + threadIdx.x; q < d1; q += T) {
-        const int c = D.ci[q] - b;
-        const int w = c >> 5;
-        const int pos = pre[w] + __popc(bm[w] & ((1u << (c & 31)) - 1u));
-        acc[pos] += beta * D.v[q];
-      }
-    }
-    __syncthreads();
-    // 5. write the row in column order; per-row sum of squares and diagonal
-    double sq = 0.0;
-    for (int k = threadIdx.x; k < cnt; k += T) {
-      int lo = 0, hi = W - 1;  // largest w with pre[w] <= k
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= k) lo = mid; else hi = mid - 1;
-      }
-      const int col = b + lo * 32 + select_bit(bm[lo], k - pre[lo]);
-      const double v = acc[k];
-      ci_out[o0 + k] = col;
-      v_out[o0 + k] = v;
-      sq += v * v;
-      if (row_diag && col == i) row_diag[i] = v;
-    }
-    if (row_sq) {
-      sq = block_sum(sq, dred);
-      if (threadIdx.x == 0) row_sq[i] = sq;
-    }
-    __syncthreads();
   }
 }
 
@@ -367,15 +639,12 @@ int num_sms() {
 void set_smem_limits() {
   static bool done = false;
   if (done) return;
-  int cap = kClassBytes[kClasses - 2];
+  const int cap = kClassBytes[kClasses - 2];
   SX_CUDA(cudaFuncSetAttribute(k_symbolic<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   SX_CUDA(cudaFuncSetAttribute(k_numeric<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   done = true;
 }
 
-}  // namespace
-
-namespace {
 struct EventPair {
   cudaEvent_t a = nullptr, b = nullptr;
   bool on;
@@ -390,7 +659,9 @@ struct EventPair {
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
   }
-  void start() { if (on) SX_CUDA(cudaEventRecord(a, s)); }
+  void start() {
+    if (on) SX_CUDA(cudaEventRecord(a, s));
+  }
   double stop() {
     if (!on) return 0.0;
     SX_CUDA(cudaEventRecord(b, s));
@@ -400,10 +671,39 @@ struct EventPair {
     return ms;
   }
 };
+
+// Owned word pattern.
+struct WPatOwned {
+  DevBuf<int64_t> rp;
+  DevBuf<int32_t> wi;
+  DevBuf<uint32_t> wb;
+  WPat view() const {
+    WPat w;
+    w.rp = rp.p; w.wi = wi.p; w.wb = wb.p;
+    return w;
+  }
+};
+
+void word_pattern(const CsrD& X, cudaStream_t s, WPatOwned& out, HostScalars& hs) {
+  const int64_t n = X.n;
+  out.rp.reset(n + 1, s);
+  DevBuf<int32_t> cnt(n, s);
+  const int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)num_sms() * 64);
+  k_wcount<<<blocks, 256, 0, s>>>(X, cnt.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+  const int64_t total = scan_counts(cnt.p, n, out.rp.p, s, hs);
+  out.wi.reset(total, s);
+  out.wb.reset(total, s);
+  k_wwrite<<<blocks, 256, 0, s>>>(X, out.rp.p, out.wi.p, out.wb.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
 }  // namespace
 
 int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, cudaStream_t s, CsrOwned& C,
-               RowStats* stats, HostScalars& hs, SpgemmTimes* times) {
+               RowStats* stats, HostScalars& hs, SpgemmTimes* times, bool upper, int64_t* done) {
   const int64_t n = A.n;
   EventPair ev_sym(times != nullptr, s), ev_num(times != nullptr, s);
   set_smem_limits();
@@ -418,19 +718,26 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
     C.nnz = 0;
     return 0;
   }
+  const bool hasD = D.n > 0;
+  const int sms = num_sms();
+  ev_sym.start();
+  WPatOwned wB, wD;
+  word_pattern(B, s, wB, hs);
+  const bool same = hasD && D.rp == B.rp && D.ci == B.ci;
+  if (hasD && !same) word_pattern(D, s, wD, hs);
+  const WPat WB = wB.view();
+  const WPat WD = hasD ? (same ? WB : wD.view()) : WPat();
   DevBuf<int32_t> base(n, s), words(n, s), cnt(n, s), lists((size_t)n * kClasses, s);
   DevBuf<int64_t> flops(n, s);
   DevBuf<unsigned long long> ctr(2 * kClasses + 4, s);
   SX_CUDA(cudaMemsetAsync(ctr.p, 0, ctr.count * sizeof(unsigned long long), s));
-  const int sms = num_sms();
-  ev_sym.start();
   {
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((n + 7) / 8, (int64_t)sms * 64);
     k_analysis<<<(unsigned)blocks, threads, 0, s>>>(A, B, D, base.p, words.p, flops.p);
     SX_CUDA(cudaGetLastError());
-    k_sum_i64<<<std::min<int64_t>((n + 255) / 256, sms * 8), 256, 0, s>>>(flops.p, n, ctr.p + 2 * kClasses + 2);
-    k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, words.p, nullptr, 0, lists.p, n, ctr.p, ctr.p + 2 * kClasses);
+    k_sum_i64<<<(unsigned)std::min<int64_t>((n + 255) / 256, sms * 8), 256, 0, s>>>(flops.p, n, ctr.p + 2 * kClasses + 2);
+    k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, words.p, nullptr, 0, lists.p, n, ctr.p, ctr.p + kClasses);
     k_zero_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(words.p, n, stats ? stats->sq.p : nullptr,
                                                          stats ? stats->diag.p : nullptr, cnt.p);
     SX_CUDA(cudaGetLastError());
@@ -447,16 +754,18 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
       const int64_t nr = (int64_t)h[c];
       if (!nr) continue;
       const int threads = kClassThreads[c];
+      const int64_t need = (int64_t)h[kClasses + c];
       if (c < kClasses - 1) {
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 32);
-        k_symbolic<false><<<(unsigned)grid, threads, kClassBytes[c], s>>>(A, B, D, lists.p + c * n, nr, base.p,
-                                                                        words.p, cnt.p, nullptr, 0);
+        const int bytes = (int)((need + 1023) & ~1023ll);
+        k_symbolic<false><<<(unsigned)grid, threads, bytes, s>>>(A, WB, WD, hasD, lists.p + c * n, nr, base.p,
+                                                               words.p, cnt.p, nullptr, 0);
       } else {
-        const int64_t stride = ((int64_t)h[2 * kClasses] / 4 + 63) & ~63ll;
+        const int64_t stride = (need / 4 + 63) & ~63ll;
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
         gs.reset((size_t)(stride * grid), s);
-        k_symbolic<true><<<(unsigned)grid, threads, 0, s>>>(A, B, D, lists.p + c * n, nr, base.p, words.p, cnt.p,
-                                                          gs.p, stride);
+        k_symbolic<true><<<(unsigned)grid, threads, 0, s>>>(A, WB, WD, hasD, lists.p + c * n, nr, base.p, words.p,
+                                                          cnt.p, gs.p, stride);
       }
       SX_CUDA(cudaGetLastError());
       count_launches(1);
@@ -465,11 +774,10 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
   // row pointers of C
   SX_CUDA(cudaMemsetAsync(ctr.p, 0, ctr.count * sizeof(unsigned long long), s));
   const int64_t total = scan_counts(cnt.p, n, C.rp.p, s, hs);
-  if (total > (int64_t)INT32_MAX * 64) fail(SEXPM_EOVERFLOW, "product too large");
   C.nnz = total;
   C.ci.reset(total, s);
   C.v.reset(total, s);
-  k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, words.p, C.rp.p, 1, lists.p, n, ctr.p, ctr.p + 2 * kClasses);
+  k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, words.p, C.rp.p, 1, lists.p, n, ctr.p, ctr.p + kClasses);
   SX_CUDA(cudaGetLastError());
   count_launches(1);
   SX_CUDA(cudaMemcpyAsync(h, ctr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -482,22 +790,41 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
       const int64_t nr = (int64_t)h[c];
       if (!nr) continue;
       const int threads = kClassThreads[c];
+      const int64_t need = (int64_t)h[kClasses + c];
       if (c < kClasses - 1) {
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 32);
-        k_numeric<false><<<(unsigned)grid, threads, kClassBytes[c], s>>>(
-            A, B, D, div, beta, lists.p + c * n, nr, base.p, words.p, C.rp.p, C.ci.p, C.v.p,
-            stats ? stats->sq.p : nullptr, stats ? stats->diag.p : nullptr, nullptr, 0);
+        const int bytes = (int)((need + 1023) & ~1023ll);
+        k_numeric<false><<<(unsigned)grid, threads, bytes, s>>>(
+            A, B, D, WB, WD, div, beta, upper, lists.p + c * n, nr, base.p, words.p, C.rp.p, C.ci.p, C.v.p,
+            stats ? stats->sq.p : nullptr, stats ? stats->diag.p : nullptr, nullptr, 0, ctr.p + 2 * kClasses + 3);
       } else {
-        const int64_t stride = ((int64_t)h[2 * kClasses] + 255) & ~255ll;
+        const int64_t stride = (need + 255) & ~255ll;
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
         gs.reset((size_t)(stride * grid), s);
-        k_numeric<true><<<(unsigned)grid, threads, 0, s>>>(A, B, D, div, beta, lists.p + c * n, nr, base.p, words.p,
-                                                         C.rp.p, C.ci.p, C.v.p, stats ? stats->sq.p : nullptr,
-                                                         stats ? stats->diag.p : nullptr, gs.p, stride);
+        k_numeric<true><<<(unsigned)grid, threads, 0, s>>>(A, B, D, WB, WD, div, beta, upper, lists.p + c * n, nr, base.p,
+                                                         words.p, C.rp.p, C.ci.p, C.v.p, stats ? stats->sq.p : nullptr,
+                                                         stats ? stats->diag.p : nullptr, gs.p, stride,
+                                                         ctr.p + 2 * kClasses + 3);
       }
       SX_CUDA(cudaGetLastError());
       count_launches(1);
     }
+  }
+  if (done) {
+    SX_CUDA(cudaMemcpyAsync(h + 2 * kClasses + 3, ctr.p + 2 * kClasses + 3, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s));
+    SX_CUDA(cudaStreamSynchronize(s));
+    *done = (int64_t)h[2 * kClasses + 3];
+  }
+  if (upper) {
+    SX_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long), s));
+    const int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)sms * 64);
+    k_mirror<<<blocks, 256, 0, s>>>(n, C.rp.p, C.ci.p, C.v.p, ctr.p);
+    SX_CUDA(cudaGetLastError());
+    count_launches(1);
+    SX_CUDA(cudaMemcpyAsync(h, ctr.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    SX_CUDA(cudaStreamSynchronize(s));
+    if (h[0] != 0) fail(SEXPM_ECUDA, "symmetric product: " + std::to_string(h[0]) + " entries without a mirror partner");
   }
   if (times) times->ms_numeric += ev_num.stop();
   return products;

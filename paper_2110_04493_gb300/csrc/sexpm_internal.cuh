@@ -117,9 +117,13 @@ struct SpgemmTimes {
 
 // C = (A B) / div + beta D.  D may have n == 0 (absent).  Allocates C; fills row
 // statistics (sum of squares, diagonal) when stats != nullptr.  Synchronises s
-// once to size C.  Returns the number of scalar products.
+// to size C.  Returns the number of scalar products.
+// upper: A, B and D are symmetric (so is C); only the products at columns >= row are
+// formed and the entries below the diagonal are copied from their mirror entries.
+// done (optional) receives the number of products actually formed.
 int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, cudaStream_t s,
-               CsrOwned& C, RowStats* stats, HostScalars& hs, SpgemmTimes* times = nullptr);
+               CsrOwned& C, RowStats* stats, HostScalars& hs, SpgemmTimes* times = nullptr, bool upper = false,
+               int64_t* done = nullptr);
 
 // sum_i x[i] over n doubles, deterministic order.  Synchronises and returns the sum.
 double reduce_sum(const double* x, int64_t n, cudaStream_t s, HostScalars& hs);
@@ -145,6 +149,9 @@ void add_identity(const CsrD& A, cudaStream_t s, CsrOwned& C, HostScalars& hs);
 
 // y[k] = alpha x[k] (values only).
 void scale_values(const double* x, double alpha, int64_t n, double* y, cudaStream_t s);
+
+// S = (A + A^T)/2 (pattern of A plus the mirrors of entries whose mirror is absent).
+void symmetric_part(const CsrD& A, cudaStream_t s, CsrOwned& S, HostScalars& hs);
 
 // A^T into T (columns sorted within rows).
 void transpose(const CsrD& A, cudaStream_t s, CsrOwned& T, HostScalars& hs);

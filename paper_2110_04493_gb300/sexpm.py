@@ -36,21 +36,23 @@ class CsrView(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("e_r", ctypes.c_double), ("square_scale", ctypes.c_int32), ("normal_override", ctypes.c_int32),
-                ("max_filter_iters", ctypes.c_int32), ("n_extra", ctypes.c_int32), ("max_taylor", ctypes.c_int32)]
+                ("max_filter_iters", ctypes.c_int32), ("n_extra", ctypes.c_int32), ("max_taylor", ctypes.c_int32),
+                ("symmetric", ctypes.c_int32)]
 
 
 class StepStats(ctypes.Structure):
     _fields_ = [("phase", ctypes.c_int32), ("i", ctypes.c_int32), ("iters", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("eps_g", ctypes.c_double), ("t", ctypes.c_double), ("b", ctypes.c_double),
                 ("norm_F", ctypes.c_double), ("nnz_raw", ctypes.c_int64), ("nnz", ctypes.c_int64),
-                ("products", ctypes.c_int64), ("ms", ctypes.c_double), ("ms_symbolic", ctypes.c_double),
+                ("products", ctypes.c_int64), ("products_done", ctypes.c_int64), ("ms", ctypes.c_double), ("ms_symbolic", ctypes.c_double),
                 ("ms_numeric", ctypes.c_double), ("ms_filter", ctypes.c_double), ("flops", ctypes.c_double),
                 ("bytes_filter", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("norm_H", ctypes.c_double), ("M", ctypes.c_int32), ("N", ctypes.c_int32),
-                ("normal", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("a", ctypes.c_double),
+                ("normal", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("symmetric", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("a", ctypes.c_double),
                 ("r0", ctypes.c_double), ("eps_g0", ctypes.c_double), ("nnz_out", ctypes.c_int64),
                 ("ms_total", ctypes.c_double), ("ms_taylor", ctypes.c_double), ("ms_squaring", ctypes.c_double),
                 ("ms_final", ctypes.c_double), ("peak_bytes", ctypes.c_int64), ("launches", ctypes.c_int64)]

@@ -155,10 +155,12 @@ def _check_method(sx, H, tau, eps, **opts):
     return res, st, so
 
 
-@pytest.mark.parametrize("name", ["lap2d_m32"])
-def test_expm_config_small_grid(sx, name):
-    c = get_config(name)
-    res, st, so = _check_method(sx, c.build(), c.tau, c.eps)
+@pytest.mark.parametrize("symmetric", [1, 0])
+def test_expm_config_small_grid(sx, symmetric):
+    """The 32x32 grid (n = 1024), with and without the symmetric (upper-triangle) products."""
+    c = get_config("lap2d_m32")
+    res, st, so = _check_method(sx, c.build(), c.tau, c.eps, symmetric=symmetric)
+    assert st["symmetric"] == symmetric
     # the per-step record: same number of squarings, kept counts within the flip allowance
     sq = [r for r in st["steps"] if r["phase"] == 1]
     assert len(sq) == so.N
@@ -167,9 +169,10 @@ def test_expm_config_small_grid(sx, name):
         assert r["eps_g"] == pytest.approx(s.eps_g, rel=1e-10)
 
 
-def test_expm_paper_toeplitz(sx):
+@pytest.mark.parametrize("symmetric", [1, 0])
+def test_expm_paper_toeplitz(sx, symmetric):
     H = toeplitz_trid(10_000, 1.0, -2.0, 1.0)
-    res, st, so = _check_method(sx, H, 1.0, 1e-16)
+    res, st, so = _check_method(sx, H, 1.0, 1e-16, symmetric=symmetric)
     assert (st["M"], st["N"]) == (20, 8)
 
 
@@ -185,7 +188,7 @@ def test_expm_3d_grid_and_nonnormal_variant(sx):
     _check_method(sx, L, tau, 1e-12)
     DL, _ = diag_scale(L, seed=1)
     res, st, so = _check_method(sx, DL, tau, 1e-12)
-    assert not st["normal"]
+    assert not st["normal"] and not st["symmetric"]
 
 
 def test_expm_absolute_threshold_option(sx):

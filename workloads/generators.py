@@ -196,5 +196,19 @@ CONFIGS: Dict[str, Config] = {
 }
 
 
-def get_config(name: str) -> Config:
-    return CONFIGS[name]
+def get_config(name: str, scale_m: int = 0) -> Config:
+    """Named workload; scale_m > 0 gives the same grid family on an m = scale_m grid with the
+    same tau/h^2 (so the same per-row kernel width) and tolerance."""
+    c = CONFIGS[name]
+    if not scale_m:
+        return c
+    if not (name.startswith("lap2d_m") or name.startswith("lap3d_m")):
+        raise ValueError("scale_m applies to the grid-Laplacian workloads only")
+    dim = 2 if name.startswith("lap2d") else 3
+    m_full = int(name.split("_m")[1].split("_")[0])
+    ratio = c.tau * (m_full + 1) ** 2
+    tau = ratio / (scale_m + 1) ** 2
+    build = (lambda: diag_scale(dirichlet_laplacian(scale_m, dim), seed=1)[0]) if name.endswith("_DL") \
+        else _lap(scale_m, dim)
+    return Config(f"{name}@m{scale_m}", build, tau, c.eps,
+                  f"{c.desc.split(',')[0]} family on a {scale_m}^{dim} grid, same tau/h^2={ratio:.4g}, eps={c.eps}")
