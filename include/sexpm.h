@@ -194,6 +194,33 @@ int sexpm_spgemm(const sexpm_csr_view* A, const sexpm_csr_view* B, const sexpm_c
 int sexpm_filter(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_iters, void* stream,
                  sexpm_result_t** out, double* t, int32_t* iters, double* b);
 
+/* ------------------------------------------------------- no-allocation call */
+
+/* Largest number of rows sexpm_filter_noalloc accepts (its fixed scratch size). */
+#define SEXPM_NOALLOC_MAX_ROWS 1048576
+
+/* Algorithm 4.1 and the compaction of the kept entries, like sexpm_filter, but without
+ * allocating any memory: no cudaMalloc/cudaFree, no pool, no pinned host buffer.  The paper
+ * has no counterpart; this call exists for callers that cannot allocate device memory when
+ * they filter, e.g. because another allocator already owns all of the GPU's memory or
+ * because they run under a fixed memory budget.
+ *
+ * A must be a device CSR (on_device = 1) with at most SEXPM_NOALLOC_MAX_ROWS rows (larger
+ * inputs return SEXPM_EOVERFLOW with a message).  The caller provides the outputs on the
+ * device: out_row_ptr (n+1 entries) and out_col / out_val with room for out_capacity
+ * entries (nnz(A) always suffices; if the kept part is larger, SEXPM_EOVERFLOW).  On success
+ * *nnz_out is the number of kept entries and t, iters and b are as for sexpm_filter.
+ *
+ * Scratch (per-row kept counts, per-block partial sums, scan tile sums; about 4.2 MB) lives
+ * in one static device array that every GPU loading the library holds until the process
+ * exits.  The first call on a device looks up its address (cudaGetSymbolAddress, once per
+ * device); make that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU race on it, so the caller must serialise them.  The call
+ * synchronises `stream` before it returns. */
+int sexpm_filter_noalloc(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_iters, void* stream,
+                         int64_t* out_row_ptr, int32_t* out_col, double* out_val, int64_t out_capacity,
+                         int64_t* nnz_out, double* t, int32_t* iters, double* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,9 @@ def load() -> ctypes.CDLL:
                                P(ctypes.c_int64)]
     L.sexpm_filter.argtypes = [P(CsrView), ctypes.c_double, ctypes.c_double, ctypes.c_int32, vp, P(vp),
                                P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_double)]
+    L.sexpm_filter_noalloc.argtypes = [P(CsrView), ctypes.c_double, ctypes.c_double, ctypes.c_int32, vp, vp, vp, vp,
+                                       ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_int32),
+                                       P(ctypes.c_double)]
     _lib = L
     return L
 
@@ -290,6 +293,30 @@ def filter_csr(A, eps_g: float, e_r: float = 0.1, max_iters: int = 100, device="
         return res.to_torch(device), t.value, it.value, b.value
     finally:
         res.free()
+
+
+NOALLOC_MAX_ROWS = 1048576
+
+
+def filter_noalloc(A, eps_g: float, e_r: float = 0.1, max_iters: int = 100, out=None):
+    """Algorithm 4.1 through sexpm_filter_noalloc, which allocates nothing itself.
+
+    A holds device tensors; `out` = (row_ptr[n+1], col[cap], val[cap]) device tensors (allocated
+    here with torch when omitted).  Returns ((row_ptr, col[:nnz], val[:nnz]), t, iters, b)."""
+    import torch
+    keep: List[Any] = []
+    a = _make_view(A, keep)
+    if out is None:
+        cap = max(1, a.nnz)
+        out = (torch.empty(a.n + 1, dtype=torch.int64, device="cuda"),
+               torch.empty(cap, dtype=torch.int32, device="cuda"),
+               torch.empty(cap, dtype=torch.float64, device="cuda"))
+    rp, ci, v = out
+    nnz, t, it, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().sexpm_filter_noalloc(ctypes.byref(a), float(eps_g), float(e_r), int(max_iters), _stream_ptr(),
+                                       rp.data_ptr(), ci.data_ptr(), v.data_ptr(), int(ci.numel()),
+                                       ctypes.byref(nnz), ctypes.byref(t), ctypes.byref(it), ctypes.byref(b)))
+    return (rp, ci[:nnz.value], v[:nnz.value]), t.value, it.value, b.value
 
 
 def kernel_launches() -> int:
