@@ -41,9 +41,19 @@ def _csr(M) -> CSR:
 
 # ------------------------------------------------------------------ the sparse product
 
-def _ragged(n, seed, dense_rows=(), empty_rows=()):
+def _sprand(n, per_row, seed):
+    """About per_row uniformly placed U[0,1) entries per row (seeded; duplicates summed)."""
     rng = np.random.default_rng(seed)
-    A = sp.random(n, n, density=min(1.0, 6.0 / n), random_state=np.random.RandomState(seed), format="lil")
+    k = max(1, int(round(per_row * n)))
+    A = sp.csr_matrix((rng.uniform(0.0, 1.0, k), (rng.integers(0, n, k), rng.integers(0, n, k))), shape=(n, n))
+    A.sum_duplicates()
+    A.sort_indices()
+    return A
+
+
+def _ragged(n, seed, dense_rows=(), empty_rows=()):
+    rng = np.random.default_rng(seed + 1000)
+    A = _sprand(n, min(6.0, n), seed).tolil()
     for r in dense_rows:
         cols = rng.choice(n, size=min(n, 3000), replace=False)
         A[r, cols] = rng.uniform(-1, 1, size=len(cols))
@@ -51,6 +61,7 @@ def _ragged(n, seed, dense_rows=(), empty_rows=()):
         A[r, :] = 0
     A = sp.csr_matrix(A)
     A.eliminate_zeros()
+    A.sort_indices()
     return A
 
 
@@ -102,7 +113,7 @@ def _assert_product_parity(G, R):
 def test_filter_matches_oracle(sx, seed):
     rng = np.random.default_rng(seed)
     n = [50, 400, 3000, 20000][seed]
-    A = sp.random(n, n, density=min(1.0, 30.0 / n), random_state=np.random.RandomState(seed), format="csr")
+    A = _sprand(n, min(30.0, n), seed)
     A.data = rng.standard_normal(A.nnz) * np.exp(rng.uniform(-45, 0, A.nnz))
     eps_g = float(np.exp(rng.uniform(-35, -15)))
     (rp, ci, v), t, iters, b = sx.filter_csr(torch_csr(_csr(A)), eps_g, 0.1)

@@ -13,9 +13,12 @@ pytestmark = pytest.mark.gpu
 
 
 def _matrix(n, seed):
+    """About 25 entries per row, values spread over 45 orders of magnitude (seeded)."""
     rng = np.random.default_rng(seed)
-    A = sp.random(n, n, density=min(1.0, 25.0 / n), random_state=np.random.RandomState(seed), format="csr")
-    A.data = rng.standard_normal(A.nnz) * np.exp(rng.uniform(-45, 0, A.nnz))
+    k = 25 * n
+    A = sp.csr_matrix((rng.standard_normal(k) * np.exp(rng.uniform(-45, 0, k)),
+                       (rng.integers(0, n, k), rng.integers(0, n, k))), shape=(n, n))
+    A.sum_duplicates()
     A.sort_indices()
     return A, float(np.exp(rng.uniform(-33, -18)))
 
