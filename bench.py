@@ -157,6 +157,47 @@ def run_reference(args):
     return 0
 
 
+def measure_batched(sexpm, torch, steps: int = 2):
+    """Batched form (256 independent 2-D Laplacians, one block-diagonal run) against the plain
+    per-matrix loop on the same GPU; inputs resident on the device for both."""
+    from workloads import BATCH_EPS, laplacian_batch
+    items = laplacian_batch()
+    devs = [(torch.from_numpy(H.row_ptr).cuda(), torch.from_numpy(H.col).cuda(), torch.from_numpy(H.val).cuda(), H.n)
+            for H, _ in items]
+    taus = [t for _, t in items]
+    bplan = sexpm.BatchedPlan(devs, BATCH_EPS)
+    for r in bplan.compute(taus):      # warm-up
+        r.free()
+    torch.cuda.synchronize()
+    l0 = sexpm.kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for r in bplan.compute(taus):
+            r.free()
+    torch.cuda.synchronize()
+    t_batched = (time.perf_counter() - t0) / steps
+    l_batched = (sexpm.kernel_launches() - l0) // steps
+    bplan.close()
+    plans = [sexpm.Plan(d, BATCH_EPS) for d in devs]
+    for p, t in zip(plans, taus):      # warm-up
+        p.compute(t).free()
+    torch.cuda.synchronize()
+    l0 = sexpm.kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for p, t in zip(plans, taus):
+            p.compute(t).free()
+    torch.cuda.synchronize()
+    t_loop = (time.perf_counter() - t0) / steps
+    l_loop = (sexpm.kernel_launches() - l0) // steps
+    for p in plans:
+        p.close()
+    return {"workload": "256 2-D Dirichlet Laplacians, side ~ U{16..128}, tau log-uniform [1e-4, 1e-2], eps 1e-12",
+            "n_total": int(sum(H.n for H, _ in items)), "batched_ms": 1000.0 * t_batched,
+            "per_matrix_loop_ms": 1000.0 * t_loop, "speedup_vs_loop": t_loop / t_batched,
+            "launches_batched": int(l_batched), "launches_loop": int(l_loop), "steps": steps}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -264,6 +305,10 @@ def run_ours(args):
         e2e = {"value": ws / e2e_s, "unit": "expm/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": int(statistics.mean(d2h_list)), "ms_per_step": 1000.0 * e2e_s}
 
+    forms = None
+    if args.forms:
+        forms = {"batched": measure_batched(sexpm, torch)}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         dt, n_s, desc = _oracle_sample(args.workload, args.sample_m)
@@ -303,7 +348,7 @@ def run_ours(args):
                           "ms_symbolic": round(r["ms_symbolic"], 3), "ms_filter": round(r["ms_filter"], 3),
                           "numeric_gflops": round(r["flops"] / (r["ms_numeric"] * 1e6), 1) if r["ms_numeric"] else None}
                          for r in st["steps"]] if args.per_step else None,
-            "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -324,6 +369,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--per-step", action="store_true", help="add the per-step records to the JSON line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", action="store_true",
+                    help="also time the batched form against the per-matrix loop (several minutes)")
     ap.add_argument("--sample-m", type=int, default=80,
                     help="grid side of the oracle's sample of the workload (same tau/h^2 and eps)")
     args = ap.parse_args(argv)

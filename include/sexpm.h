@@ -175,6 +175,22 @@ double sexpm_rho(int32_t M, double x);
  * M + N, then the smaller N.  norm_H = 0 gives M = N = 0. */
 int sexpm_choose_MN(double norm_H, double eps, int32_t n_extra, int32_t max_M, int32_t* M, int32_t* N);
 
+/* ---------------------------------------------------------- batched form */
+
+/* Many independent matrices H_b (b = 0..count-1, sizes may differ) planned together: the
+ * instances are stored as one block-diagonal matrix, so every step of Algorithm 4.2 runs as one
+ * set of kernel launches for the whole batch.  Validation, symmetry and normality are per
+ * instance.  eps is shared.  Not in the paper (the benchmark spec's batched form of Algorithm 4.2). */
+int sexpm_plan_batched(const sexpm_csr_view* Hs, int32_t count, double eps, const sexpm_options* opt,
+                       void* stream, sexpm_plan_t** out);
+
+/* Algorithm 4.2 for every tau_b H_b of a batched plan: each instance gets its own (M_b, N_b)
+ * by Eq. (4.20), its own a_b, r_0 and thresholds, and its own Algorithm 4.1 iterations; an
+ * instance that has done its N_b squarings is carried unchanged through the remaining
+ * steps.  outs[b] receives e^{tau_b H_b} (an n_b x n_b result).  For a plain plan this
+ * is sexpm_compute with taus[0]. */
+int sexpm_compute_batched(sexpm_plan_t* plan, const double* taus, sexpm_result_t** outs);
+
 /* ------------------------------------------------------------ step calls */
 /* The individual steps of the hot path on caller-provided device CSR views,
  * for testing and measurement.  Outputs are new result handles. */

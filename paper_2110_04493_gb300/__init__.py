@@ -5,11 +5,13 @@ The compute path lives in libsexpm.so (CUDA kernels behind the C ABI of
 include/sexpm.h); :mod:`paper_2110_04493_gb300.sexpm` is its Python binding.
 """
 from .sexpm import (  # noqa: F401
+    BatchedPlan,
     Plan,
     Result,
     SexpmError,
     choose_MN,
     expm,
+    expm_batched,
     filter_csr,
     load,
     rho,

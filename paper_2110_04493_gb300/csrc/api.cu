@@ -205,6 +205,92 @@ void copy_csr(const CsrD& A, cudaStream_t s, CsrOwned& out) {
   }
 }
 
+// Algorithm 4.2 step 2: exact symmetry, and normality (H = H^T or H = -H^T exactly, else
+// ||H H^T - H^T H||_F <= 64 u ||H||_F^2), unless overridden.
+void classify_matrix(const CsrOwned& H, int normal_override, cudaStream_t s, HostScalars& hs, bool& symmetric,
+                     int& normal) {
+  CsrOwned Ht;
+  transpose(H.view(), s, Ht, hs);
+  symmetric = csr_equal(H.view(), Ht.view(), 1.0, s, hs);
+  if (normal_override >= 0) {
+    normal = normal_override;
+  } else if (symmetric || csr_equal(H.view(), Ht.view(), -1.0, s, hs)) {
+    normal = 1;
+  } else {
+    CsrOwned P, Q, C;
+    CsrD none;
+    spgemm(H.view(), Ht.view(), none, 1.0, 0.0, s, P, nullptr, hs);
+    spgemm(Ht.view(), H.view(), none, 1.0, 0.0, s, Q, nullptr, hs);
+    add(P.view(), Q.view(), -1.0, s, C, hs);
+    const double nc = std::sqrt(sum_squares(C.view(), s, hs));
+    const double nh2 = sum_squares(H.view(), s, hs);
+    normal = nc <= 64.0 * std::ldexp(1.0, -53) * nh2 ? 1 : 0;
+  }
+}
+
+struct SegFilterOut {
+  std::vector<double> t, b;
+  std::vector<int> iters;
+  double ms = 0.0;
+};
+
+// Algorithm 4.1 run independently for every instance of a block-diagonal matrix: instance b
+// uses bound eps_g[b]; instances with fixed[b] >= 0 are not iterated and use t = fixed[b]
+// (0 keeps every nonzero entry, +inf drops every entry).  One device pass serves all
+// unconverged instances; then A~ = A - b_n into `out`.
+SegFilterOut filter_seg(const CsrD& A, const std::vector<double>& eps_g, const std::vector<double>& fixed, double e_r,
+                        int max_iters, const int32_t* inst, const int64_t* seg, int count, cudaStream_t s,
+                        CsrOwned& out, HostScalars& hs) {
+  SegFilterOut r;
+  Timer tf(s);
+  r.t.assign(count, 0.0);
+  r.b.assign(count, 0.0);
+  r.iters.assign(count, 0);
+  std::vector<double> m(count, 1.0), sums(count, 0.0);
+  std::vector<char> conv(count, 0);
+  for (int k = 0; k < count; ++k) {
+    if (fixed[k] >= 0.0) {
+      conv[k] = 1;
+      r.t[k] = fixed[k];
+    } else {
+      r.t[k] = eps_g[k];
+      r.b[k] = std::numeric_limits<double>::infinity();
+    }
+  }
+  DevBuf<int32_t> keep(A.n ? A.n : 1, s);
+  DevBuf<double> part(A.n ? A.n : 1, s), tdev(count, s);
+  while (true) {
+    for (int k = 0; k < count; ++k)
+      if (!conv[k]) r.t[k] = eps_g[k] / m[k];
+    SX_CUDA(cudaMemcpyAsync(tdev.p, r.t.data(), count * sizeof(double), cudaMemcpyHostToDevice, s));
+    filter_pass_seg(A, inst, tdev.p, keep.p, part.p, seg, count, sums.data(), s);
+    bool all = true;
+    for (int k = 0; k < count; ++k) {
+      if (conv[k]) continue;
+      r.b[k] = std::sqrt(sums[k]);
+      m[k] = r.b[k] / r.t[k];
+      ++r.iters[k];
+      if (r.b[k] <= eps_g[k] * (1.0 + e_r)) {
+        conv[k] = 1;
+      } else {
+        all = false;
+        if (r.iters[k] >= max_iters)
+          fail(SEXPM_ENOCONV, "Algorithm 4.1 did not converge within " + std::to_string(max_iters) +
+                                  " passes (instance " + std::to_string(k) + ")");
+      }
+    }
+    if (all) break;
+  }
+  out.n = A.n;
+  out.rp.reset(A.n + 1, s);
+  out.nnz = scan_counts(keep.p, A.n, out.rp.p, s, hs);
+  out.ci.reset(out.nnz, s);
+  out.v.reset(out.nnz, s);
+  compact_seg(A, inst, tdev.p, out, s);
+  r.ms = tf.ms();
+  return r;
+}
+
 }  // namespace
 }  // namespace sexpm
 
@@ -219,6 +305,13 @@ struct sexpm_plan {
   int normal = 1;
   bool symmetric = false;  // H == H^T exactly
   HostScalars hs;
+  // batched plans (count > 0): H is block diagonal, instance b owns rows row0[b] .. row0[b+1]
+  int32_t count = 0;
+  std::vector<int64_t> row0;
+  std::vector<int> normal_b;
+  std::vector<char> symmetric_b;
+  DevBuf<int64_t> seg;
+  DevBuf<int32_t> inst;
 };
 
 struct sexpm_result {
@@ -294,26 +387,7 @@ int sexpm_plan(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_optio
     p->s = static_cast<cudaStream_t>(stream);
     p->eps = eps;
     upload(*H, p->s, p->H, p->hs);
-    CsrOwned Ht;
-    transpose(p->H.view(), p->s, Ht, p->hs);
-    p->symmetric = csr_equal(p->H.view(), Ht.view(), 1.0, p->s, p->hs);
-    if (p->opt.normal_override >= 0) {
-      p->normal = p->opt.normal_override;
-    } else {
-      // Algorithm 4.2 step 2: normality.  Exact symmetry / skew-symmetry first.
-      if (p->symmetric || csr_equal(p->H.view(), Ht.view(), -1.0, p->s, p->hs)) {
-        p->normal = 1;
-      } else {
-        CsrOwned P, Q, C;
-        CsrD none;
-        spgemm(p->H.view(), Ht.view(), none, 1.0, 0.0, p->s, P, nullptr, p->hs);
-        spgemm(Ht.view(), p->H.view(), none, 1.0, 0.0, p->s, Q, nullptr, p->hs);
-        add(P.view(), Q.view(), -1.0, p->s, C, p->hs);
-        const double nc = std::sqrt(sum_squares(C.view(), p->s, p->hs));
-        const double nh2 = sum_squares(p->H.view(), p->s, p->hs);
-        p->normal = nc <= 64.0 * std::ldexp(1.0, -53) * nh2 ? 1 : 0;
-      }
-    }
+    classify_matrix(p->H, p->opt.normal_override, p->s, p->hs, p->symmetric, p->normal);
     SX_CUDA(cudaStreamSynchronize(p->s));
   } catch (...) {
     delete p;
@@ -328,6 +402,7 @@ int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
   if (!p || !out) fail(SEXPM_EINVAL, "null argument");
   *out = nullptr;
   if (!std::isfinite(tau)) fail(SEXPM_EINVAL, "tau must be finite");
+  if (p->count > 0) fail(SEXPM_EINVAL, "batched plan: use sexpm_compute_batched");
   int dev = 0;
   SX_CUDA(cudaGetDevice(&dev));
   if (dev != p->device) fail(SEXPM_EINVAL, "current device differs from the plan's device");
@@ -608,6 +683,299 @@ int sexpm_filter(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_
     throw;
   }
   *out = res;
+  SX_API_END
+}
+
+int sexpm_plan_batched(const sexpm_csr_view* Hs, int32_t count, double eps, const sexpm_options* opt, void* stream,
+                       sexpm_plan_t** out) {
+  SX_API_BEGIN
+  if (!Hs || !out || count < 1) fail(SEXPM_EINVAL, "need count >= 1 matrices");
+  *out = nullptr;
+  if (!(eps > 0.0) || !std::isfinite(eps)) fail(SEXPM_EINVAL, "eps must be positive and finite");
+  sexpm_plan_t* p = new sexpm_plan_t();
+  try {
+    if (opt) p->opt = *opt; else sexpm_options_default(&p->opt);
+    check_options(p->opt);
+    SX_CUDA(cudaGetDevice(&p->device));
+    p->s = static_cast<cudaStream_t>(stream);
+    p->eps = eps;
+    p->count = count;
+    cudaStream_t s = p->s;
+    p->row0.assign(count + 1, 0);
+    std::vector<int64_t> nz0(count + 1, 0);
+    for (int b = 0; b < count; ++b) {
+      if (Hs[b].n < 0 || Hs[b].nnz < 0) fail(SEXPM_EINVAL, "bad dimensions of instance " + std::to_string(b));
+      p->row0[b + 1] = p->row0[b] + Hs[b].n;
+      nz0[b + 1] = nz0[b] + Hs[b].nnz;
+    }
+    if (p->row0[count] > INT32_MAX) fail(SEXPM_EOVERFLOW, "the batch has more than 2^31 rows");
+    const int64_t n = p->row0[count], nnz = nz0[count];
+    p->H.n = n;
+    p->H.nnz = nnz;
+    p->H.rp.reset(n + 1, s);
+    p->H.ci.reset(nnz, s);
+    p->H.v.reset(nnz, s);
+    p->normal_b.assign(count, 1);
+    p->symmetric_b.assign(count, 1);
+    for (int b = 0; b < count; ++b) {
+      CsrOwned Hb;
+      upload(Hs[b], s, Hb, p->hs);
+      bool sym = false;
+      int nor = 1;
+      classify_matrix(Hb, p->opt.normal_override, s, p->hs, sym, nor);
+      p->symmetric_b[b] = sym ? 1 : 0;
+      p->normal_b[b] = nor;
+      block_put(Hb.view(), p->row0[b], nz0[b], p->H.rp.p, p->H.ci.p, p->H.v.p, s);
+      SX_CUDA(cudaStreamSynchronize(s));
+    }
+    SX_CUDA(cudaMemcpyAsync(p->H.rp.p + n, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    p->seg.reset(count + 1, s);
+    SX_CUDA(cudaMemcpyAsync(p->seg.p, p->row0.data(), (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    p->inst.reset(n ? n : 1, s);
+    instance_of_row(p->seg.p, count, n, p->inst.p, s);
+    p->symmetric = true;
+    for (int b = 0; b < count; ++b) p->symmetric = p->symmetric && p->symmetric_b[b];
+    SX_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    delete p;
+    throw;
+  }
+  *out = p;
+  SX_API_END
+}
+
+int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** outs) {
+  SX_API_BEGIN
+  if (!p || !taus || !outs) fail(SEXPM_EINVAL, "null argument");
+  if (p->count == 0) {
+    const int rc = sexpm_compute(p, taus[0], outs);
+    if (rc != SEXPM_OK) return rc;
+    set_last_error("");
+    return SEXPM_OK;
+  }
+  const int count = p->count;
+  for (int b = 0; b < count; ++b) {
+    outs[b] = nullptr;
+    if (!std::isfinite(taus[b])) fail(SEXPM_EINVAL, "tau of instance " + std::to_string(b) + " is not finite");
+  }
+  int dev = 0;
+  SX_CUDA(cudaGetDevice(&dev));
+  if (dev != p->device) fail(SEXPM_EINVAL, "current device differs from the plan's device");
+  cudaStream_t s = p->s;
+  HostScalars& hs = p->hs;
+  const sexpm_options& o = p->opt;
+  const int64_t n = p->H.n;
+  const int32_t* inst = p->inst.p;
+  const int64_t* seg = p->seg.p;
+  Pool::reset_peak();
+  const int64_t live0 = Pool::live();
+  const int64_t launches0 = launches();
+  Timer t_all(s);
+  std::vector<sexpm_step_stats> steps;
+  // step 1: tau_b H_b, ||tau_b H_b||_F, (M_b, N_b)
+  DevBuf<double> dtmp(count, s);
+  SX_CUDA(cudaMemcpyAsync(dtmp.p, taus, count * sizeof(double), cudaMemcpyHostToDevice, s));
+  DevBuf<double> hv(p->H.nnz, s);
+  CsrD Hs = p->H.view();
+  scale_rows(Hs, inst, dtmp.p, hv.p, s);
+  Hs.v = hv.p;
+  std::vector<double> sums(count, 0.0), normH(count), a(count), r0(count), eps_g0(count), x0(count);
+  std::vector<int32_t> M(count), N(count);
+  {
+    DevBuf<int32_t> keep(n ? n : 1, s);
+    DevBuf<double> part(n ? n : 1, s);
+    std::vector<double> inf(count, std::numeric_limits<double>::infinity());
+    SX_CUDA(cudaMemcpyAsync(dtmp.p, inf.data(), count * sizeof(double), cudaMemcpyHostToDevice, s));
+    filter_pass_seg(Hs, inst, dtmp.p, keep.p, part.p, seg, count, sums.data(), s);
+  }
+  int32_t Mmax = 0, Nmax = 0;
+  for (int b = 0; b < count; ++b) {
+    normH[b] = std::sqrt(sums[b]);
+    const int rc = sexpm_choose_MN(normH[b], p->eps, o.n_extra, o.max_taylor, &M[b], &N[b]);
+    if (rc != SEXPM_OK) fail(rc, "no feasible (M, N) for instance " + std::to_string(b));
+    const bool nor = p->normal_b[b] != 0 || normH[b] == 0.0;
+    a[b] = nor ? 1.0 / (1.0 + N[b]) : 1.0 / normH[b];
+    x0[b] = std::ldexp(normH[b], -N[b]);
+    r0[b] = M[b] > 0 ? sexpm_rho(M[b], x0[b]) : 0.0;
+    eps_g0[b] = M[b] > 0 ? a[b] * r0[b] / ((double)M[b] * std::exp(2.0 * x0[b])) : 0.0;
+    Mmax = std::max(Mmax, M[b]);
+    Nmax = std::max(Nmax, N[b]);
+  }
+  const bool sym = p->symmetric && o.symmetric;
+  // step 3: Taylor phase for all instances at once
+  Timer t_tay(s);
+  std::vector<double> fac(count);
+  for (int b = 0; b < count; ++b) fac[b] = std::ldexp(1.0, -N[b]);
+  SX_CUDA(cudaMemcpyAsync(dtmp.p, fac.data(), count * sizeof(double), cudaMemcpyHostToDevice, s));
+  DevBuf<double> h0v(p->H.nnz, s);
+  scale_rows(Hs, inst, dtmp.p, h0v.p, s);
+  CsrD H0 = Hs;
+  H0.v = h0v.p;
+  CsrOwned T;
+  copy_csr(H0, s, T);
+  CsrOwned S;
+  CsrD Sv = H0;
+  CsrD none;
+  std::vector<char> done_b(count, 0);
+  for (int b = 0; b < count; ++b) done_b[b] = M[b] <= 1;
+  std::vector<int64_t> bnd(count + 1);
+  const double inf = std::numeric_limits<double>::infinity();
+  for (int i = 2; i <= Mmax; ++i) {
+    Timer ts(s);
+    CsrOwned St;
+    SpgemmTimes tm;
+    int64_t done = 0;
+    const int64_t prod = spgemm(Sv, H0, none, (double)i, 0.0, s, St, nullptr, hs, &tm, false, &done);
+    std::vector<double> eg(count), fixed(count, -1.0);
+    for (int b = 0; b < count; ++b) {
+      eg[b] = eps_g0[b];
+      if (done_b[b] || i > M[b]) fixed[b] = inf;
+    }
+    CsrOwned Sn;
+    SegFilterOut fo = filter_seg(St.view(), eg, fixed, o.e_r, o.max_filter_iters, inst, seg, count, s, Sn, hs);
+    gather_row_ptr(Sn.rp.p, seg, count, bnd.data(), s);
+    for (int b = 0; b < count; ++b)
+      if (bnd[b + 1] == bnd[b]) done_b[b] = 1;
+    sexpm_step_stats rec;
+    std::memset(&rec, 0, sizeof(rec));
+    rec.phase = 0;
+    rec.i = i;
+    for (int b = 0; b < count; ++b) {
+      rec.iters = std::max(rec.iters, fo.iters[b]);
+      if (fixed[b] < 0.0) rec.t = std::max(rec.t, fo.t[b]);
+    }
+    rec.nnz_raw = St.nnz;
+    rec.nnz = Sn.nnz;
+    rec.products = prod;
+    rec.products_done = done;
+    rec.ms_symbolic = tm.ms_symbolic;
+    rec.ms_numeric = tm.ms_numeric;
+    rec.ms_filter = fo.ms;
+    rec.flops = 2.0 * (double)done + (double)St.nnz;
+    if (Sn.nnz == 0) {
+      rec.ms = ts.ms();
+      steps.push_back(rec);
+      break;
+    }
+    CsrOwned Tn;
+    add(T.view(), Sn.view(), 1.0, s, Tn, hs);
+    T = std::move(Tn);
+    S = std::move(Sn);
+    Sv = S.view();
+    rec.ms = ts.ms();
+    steps.push_back(rec);
+  }
+  S.rp.free(); S.ci.free(); S.v.free();
+  if (sym) {
+    CsrOwned Ts;
+    symmetric_part(T.view(), s, Ts, hs);
+    T = std::move(Ts);
+  }
+  const double ms_taylor = t_tay.ms();
+  // step 4: squarings; instance b is frozen (copied through) once its N_b squarings are done
+  Timer t_sq(s);
+  RowStats rs;
+  DevBuf<uint8_t> frozen_inst(count, s), frozen_row(n ? n : 1, s);
+  std::vector<uint8_t> fz(count);
+  std::vector<double> sq(count), tr(count);
+  for (int g = 1; g <= Nmax; ++g) {
+    Timer ts(s);
+    for (int b = 0; b < count; ++b) fz[b] = N[b] < g ? 1 : 0;
+    SX_CUDA(cudaMemcpyAsync(frozen_inst.p, fz.data(), count, cudaMemcpyHostToDevice, s));
+    row_flags(inst, frozen_inst.p, n, frozen_row.p, s);
+    CsrOwned Tt;
+    SpgemmTimes tm;
+    int64_t done = 0;
+    const int64_t prod = spgemm(T.view(), T.view(), T.view(), 1.0, 2.0, s, Tt, &rs, hs, &tm, sym, &done, frozen_row.p);
+    std::vector<double> eg(count, 0.0), fixed(count, -1.0);
+    if (o.square_scale) {
+      seg_sums(rs.sq.p, seg, count, sq.data(), s);
+      seg_sums(rs.diag.p, seg, count, tr.data(), s);
+    }
+    for (int b = 0; b < count; ++b) {
+      if (fz[b]) {
+        fixed[b] = 0.0;  // keep every stored nonzero: the instance is finished
+        continue;
+      }
+      double normF = 1.0;
+      if (o.square_scale) {
+        const double f2 = sq[b] + (double)(p->row0[b + 1] - p->row0[b]) + 2.0 * tr[b];
+        normF = std::sqrt(f2 > 0.0 ? f2 : 0.0);
+      }
+      eg[b] = a[b] * std::ldexp(r0[b], g) * normF;
+    }
+    const double flops = 2.0 * (double)done + 2.0 * (double)T.nnz;
+    T.rp.free(); T.ci.free(); T.v.free();
+    CsrOwned Tn;
+    SegFilterOut fo = filter_seg(Tt.view(), eg, fixed, o.e_r, o.max_filter_iters, inst, seg, count, s, Tn, hs);
+    sexpm_step_stats rec;
+    std::memset(&rec, 0, sizeof(rec));
+    rec.phase = 1;
+    rec.i = g;
+    for (int b = 0; b < count; ++b) {
+      rec.iters = std::max(rec.iters, fo.iters[b]);
+      if (fixed[b] < 0.0) {
+        rec.t = std::max(rec.t, fo.t[b]);
+        rec.eps_g = std::max(rec.eps_g, eg[b]);
+      }
+    }
+    rec.nnz_raw = Tt.nnz;
+    rec.nnz = Tn.nnz;
+    rec.products = prod;
+    rec.products_done = done;
+    rec.ms_symbolic = tm.ms_symbolic;
+    rec.ms_numeric = tm.ms_numeric;
+    rec.ms_filter = fo.ms;
+    rec.flops = flops;
+    Tt.rp.free(); Tt.ci.free(); Tt.v.free();
+    T = std::move(Tn);
+    rec.ms = ts.ms();
+    steps.push_back(rec);
+  }
+  const double ms_squaring = t_sq.ms();
+  // step 5: e^{tau_b H_b} = I + T^_{N_b}, then one result per instance
+  Timer t_fin(s);
+  CsrOwned E;
+  add_identity(T.view(), s, E, hs);
+  T.rp.free(); T.ci.free(); T.v.free();
+  gather_row_ptr(E.rp.p, seg, count, bnd.data(), s);
+  std::vector<sexpm_result*> res(count, nullptr);
+  try {
+    for (int b = 0; b < count; ++b) {
+      res[b] = new sexpm_result();
+      res[b]->s = s;
+      block_get(E.view(), p->row0[b], p->row0[b + 1] - p->row0[b], bnd[b + 1] - bnd[b], res[b]->E, s);
+    }
+    SX_CUDA(cudaStreamSynchronize(s));
+    const double ms_final = t_fin.ms();
+    const double ms_total = t_all.ms();
+    for (int b = 0; b < count; ++b) {
+      sexpm_stats_t& st = res[b]->st;
+      std::memset(&st, 0, sizeof(st));
+      st.n = p->row0[b + 1] - p->row0[b];
+      st.norm_H = normH[b];
+      st.M = M[b];
+      st.N = N[b];
+      st.normal = (p->normal_b[b] != 0 || normH[b] == 0.0) ? 1 : 0;
+      st.symmetric = sym ? 1 : 0;
+      st.a = M[b] ? a[b] : 0.0;
+      st.r0 = r0[b];
+      st.eps_g0 = eps_g0[b];
+      st.nnz_out = res[b]->E.nnz;
+      st.ms_total = ms_total;
+      st.ms_taylor = ms_taylor;
+      st.ms_squaring = ms_squaring;
+      st.ms_final = ms_final;
+      st.peak_bytes = Pool::peak() - live0;
+      st.launches = launches() - launches0;
+      res[b]->steps = steps;
+      st.n_steps = (int32_t)steps.size();
+    }
+  } catch (...) {
+    for (auto* r : res) delete r;
+    throw;
+  }
+  for (int b = 0; b < count; ++b) outs[b] = res[b];
   SX_API_END
 }
 

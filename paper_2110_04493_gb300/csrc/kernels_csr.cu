@@ -325,6 +325,119 @@ __global__ void k_sort_rows(int64_t n, const int64_t* rp, int32_t* ci, double* v
   }
 }
 
+
+// ---- batched (block-diagonal) helpers: inst[i] is the instance of row i; instances own
+//      contiguous row ranges seg[b] .. seg[b+1]
+
+// Algorithm 4.1 pass with a threshold per instance: row_part[i] = sum_{|v| <= t_inst} v^2 over
+// row i, keep[i] = #{|v| > t_inst}.  One warp per row.
+__global__ void k_filter_pass_seg(CsrD A, const int32_t* inst, const double* t_inst, int32_t* keep, double* row_part) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
+    const double t = t_inst[inst[i]];
+    int c = 0;
+    double sq = 0.0;
+    for (int64_t q = A.rp[i] + lane_id(); q < A.rp[i + 1]; q += 32) {
+      const double v = A.v[q];
+      if (fabs(v) > t) ++c; else sq += v * v;
+    }
+    c = warp_sum(c);
+    sq = warp_sum(sq);
+    if (lane_id() == 0) {
+      keep[i] = c;
+      row_part[i] = sq;
+    }
+  }
+}
+
+// out[b] = sum of x over the rows of instance b (one block per instance, fixed order).
+__global__ void k_seg_sum(const double* x, const int64_t* seg, double* out) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = seg[b] + threadIdx.x; i < seg[b + 1]; i += blockDim.x) s += x[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[b] = s;
+}
+
+__global__ void k_compact_seg(CsrD A, const int32_t* inst, const double* t_inst, const int64_t* rp_out, int32_t* ci_out,
+                              double* v_out) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const unsigned lt = (1u << lane_id()) - 1u;
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
+    const double t = t_inst[inst[i]];
+    const int64_t q0 = A.rp[i], q1 = A.rp[i + 1];
+    int64_t o = rp_out[i];
+    for (int64_t qb = q0; qb < q1; qb += 32) {
+      const int64_t q = qb + lane_id();
+      const bool act = q < q1;
+      const double v = act ? A.v[q] : 0.0;
+      const bool keep = act && fabs(v) > t;
+      const unsigned m = __ballot_sync(FULL, keep);
+      if (keep) {
+        const int64_t d = o + __popc(m & lt);
+        ci_out[d] = A.ci[q];
+        v_out[d] = v;
+      }
+      o += __popc(m);
+    }
+  }
+}
+
+// out_v = factor[inst[row]] * v, one warp per row.
+__global__ void k_scale_rows(CsrD A, const int32_t* inst, const double* factor, double* out_v) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
+    const double f = factor[inst[i]];
+    for (int64_t q = A.rp[i] + lane_id(); q < A.rp[i + 1]; q += 32) out_v[q] = f * A.v[q];
+  }
+}
+
+// Instance of every row: the largest b with seg[b] <= i.
+__global__ void k_instance_of_row(const int64_t* seg, int count, int64_t n, int32_t* inst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  inst[i] = lo;
+}
+
+// Row flag from an instance flag.
+__global__ void k_row_flags(const int32_t* inst, const uint8_t* inst_flag, int64_t n, uint8_t* row_flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) row_flag[i] = inst_flag[inst[i]];
+}
+
+// Copy instance block X (n_b rows) into the block-diagonal arrays at (row0, nnz0).
+__global__ void k_block_put(CsrD X, int64_t row0, int64_t nnz0, int64_t* rp, int32_t* ci, double* v) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < X.n; i += stride) rp[row0 + i] = X.rp[i] + nnz0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < X.nnz; q += stride) {
+    ci[nnz0 + q] = X.ci[q] + (int)row0;
+    v[nnz0 + q] = X.v[q];
+  }
+}
+
+// Rows [row0, row0 + nb) of E as an nb x nb CSR (columns shifted by -row0).
+__global__ void k_block_get(CsrD E, int64_t row0, int64_t nb, int64_t* rp, int32_t* ci, double* v) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nnz0 = E.rp[row0];
+  const int64_t nnz1 = E.rp[row0 + nb];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= nb; i += stride) rp[i] = E.rp[row0 + i] - nnz0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz1 - nnz0; q += stride) {
+    ci[q] = E.ci[nnz0 + q] - (int)row0;
+    v[q] = E.v[nnz0 + q];
+  }
+}
+
+__global__ void k_gather_rp(const int64_t* rp, const int64_t* seg, int count, int64_t* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b <= count) out[b] = rp[seg[b]];
+}
+
 // ---- symmetric part: (A + A^T)/2 on the pattern of A; entries whose mirror is absent are flagged
 __device__ __forceinline__ int64_t lb_col(const int32_t* ci, int64_t lo, int64_t hi, int c) {
   while (lo < hi) {
@@ -553,6 +666,90 @@ void transpose(const CsrD& A, cudaStream_t s, CsrOwned& T, HostScalars& hs) {
     count_launches(2);
   }
   SX_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- batched helpers (host)
+
+void seg_sums(const double* x, const int64_t* seg, int count, double* out_host, cudaStream_t s) {
+  if (count == 0) return;
+  DevBuf<double> out(count, s);
+  k_seg_sum<<<count, 256, 0, s>>>(x, seg, out.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+  SX_CUDA(cudaMemcpyAsync(out_host, out.p, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SX_CUDA(cudaStreamSynchronize(s));
+}
+
+void filter_pass_seg(const CsrD& A, const int32_t* inst, const double* t_inst, int32_t* keep, double* row_part,
+                     const int64_t* seg, int count, double* sums_host, cudaStream_t s) {
+  if (A.n) {
+    const int blocks = (int)std::min<int64_t>((A.n + 7) / 8, (int64_t)sm_count() * 64);
+    k_filter_pass_seg<<<blocks, 256, 0, s>>>(A, inst, t_inst, keep, row_part);
+    SX_CUDA(cudaGetLastError());
+    count_launches(1);
+  }
+  seg_sums(row_part, seg, count, sums_host, s);
+}
+
+void compact_seg(const CsrD& A, const int32_t* inst, const double* t_inst, CsrOwned& C, cudaStream_t s) {
+  if (A.n == 0) return;
+  const int blocks = (int)std::min<int64_t>((A.n + 7) / 8, (int64_t)sm_count() * 64);
+  k_compact_seg<<<blocks, 256, 0, s>>>(A, inst, t_inst, C.rp.p, C.ci.p, C.v.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+void scale_rows(const CsrD& A, const int32_t* inst, const double* factor, double* out_v, cudaStream_t s) {
+  if (A.n == 0) return;
+  const int blocks = (int)std::min<int64_t>((A.n + 7) / 8, (int64_t)sm_count() * 64);
+  k_scale_rows<<<blocks, 256, 0, s>>>(A, inst, factor, out_v);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+void instance_of_row(const int64_t* seg, int count, int64_t n, int32_t* inst, cudaStream_t s) {
+  if (n == 0) return;
+  k_instance_of_row<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seg, count, n, inst);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+void row_flags(const int32_t* inst, const uint8_t* inst_flag, int64_t n, uint8_t* row_flag, cudaStream_t s) {
+  if (n == 0) return;
+  k_row_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(inst, inst_flag, n, row_flag);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+void block_put(const CsrD& X, int64_t row0, int64_t nnz0, int64_t* rp, int32_t* ci, double* v, cudaStream_t s) {
+  const int64_t work = std::max<int64_t>(X.n, X.nnz);
+  if (work == 0) return;
+  const int blocks = (int)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count() * 16);
+  k_block_put<<<blocks, 256, 0, s>>>(X, row0, nnz0, rp, ci, v);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+void block_get(const CsrD& E, int64_t row0, int64_t nb, int64_t nnz_b, CsrOwned& out, cudaStream_t s) {
+  out.n = nb;
+  out.nnz = nnz_b;
+  out.rp.reset(nb + 1, s);
+  out.ci.reset(nnz_b, s);
+  out.v.reset(nnz_b, s);
+  const int64_t work = std::max<int64_t>(nb + 1, nnz_b);
+  const int blocks = (int)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count() * 16);
+  k_block_get<<<blocks, 256, 0, s>>>(E, row0, nb, out.rp.p, out.ci.p, out.v.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+void gather_row_ptr(const int64_t* rp, const int64_t* seg, int count, int64_t* out_host, cudaStream_t s) {
+  DevBuf<int64_t> out(count + 1, s);
+  k_gather_rp<<<(count + 256) / 256, 256, 0, s>>>(rp, seg, count, out.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+  SX_CUDA(cudaMemcpyAsync(out_host, out.p, (count + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SX_CUDA(cudaStreamSynchronize(s));
 }
 
 void symmetric_part(const CsrD& A, cudaStream_t s, CsrOwned& S, HostScalars& hs) {

@@ -192,12 +192,14 @@ __global__ void k_wwrite(CsrD X, const int64_t* wrp, int32_t* wi, uint32_t* wb) 
 // ---------------------------------------------------------------- row analysis and binning
 // Per row: column span of the product row (A B plus the pattern of D) and its product count.
 // One warp per row.
-__global__ void k_analysis(CsrD A, CsrD B, CsrD D, int32_t* base, int32_t* words, int64_t* flops) {
+__global__ void k_analysis(CsrD A, CsrD B, CsrD D, const uint8_t* frozen, int32_t* base, int32_t* words,
+                           int64_t* flops) {
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
     int lo = INT_MAX, hi = -1;
     int64_t f = 0;
-    const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
+    const bool fz = frozen && frozen[i];
+    const int64_t a0 = A.rp[i], a1 = fz ? a0 : A.rp[i + 1];
     for (int64_t p = a0 + lane_id(); p < a1; p += 32) {
       const int k = A.ci[p];
       const int64_t b0 = B.rp[k], b1 = B.rp[k + 1];
@@ -275,9 +277,9 @@ __global__ void k_classify(int64_t n, const int32_t* words, const int64_t* rp_ou
 // Block-wide; the caller synchronises afterwards.
 // With upper set, only products at columns >= i are counted as work.
 __device__ __forceinline__ void build_row_bitmap(const CsrD& A, const WPat& WB, const WPat& WD, bool hasD, int64_t i,
-                                                 int wlo, uint32_t* bm, unsigned* work, bool upper) {
+                                                 int wlo, uint32_t* bm, unsigned* work, bool upper, bool fz) {
   const int nwarps = blockDim.x >> 5;
-  const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
+  const int64_t a0 = A.rp[i], a1 = fz ? a0 : A.rp[i + 1];
   const int iw = (int)(i >> 5);
   const uint32_t imask = ~((1u << (i & 31)) - 1u);
   for (int64_t p = a0 + warp_id(); p < a1; p += nwarps) {
@@ -342,8 +344,8 @@ __device__ unsigned block_exclusive_scan(unsigned* x, int W, unsigned* red) {
 
 // Symbolic pass: cnt[i] = number of distinct columns of row i of A B (+ pattern of D).
 template <bool GLOBAL>
-__global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const int32_t* rows, int64_t nrows,
-                           const int32_t* base, const int32_t* words, int32_t* cnt, uint32_t* gscratch,
+__global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const uint8_t* frozen, const int32_t* rows,
+                           int64_t nrows, const int32_t* base, const int32_t* words, int32_t* cnt, uint32_t* gscratch,
                            int64_t gstride) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int red[32];
@@ -354,7 +356,7 @@ __global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const int32_t* r
     const int wlo = base[i] >> 5;
     for (int w = threadIdx.x; w < W; w += blockDim.x) bm[w] = 0u;
     __syncthreads();
-    build_row_bitmap(A, WB, WD, hasD, i, wlo, bm, nullptr, false);
+    build_row_bitmap(A, WB, WD, hasD, i, wlo, bm, nullptr, false, frozen && frozen[i]);
     __syncthreads();
     int c = 0;
     for (int w = threadIdx.x; w < W; w += blockDim.x) c += __popc(bm[w]);
@@ -403,8 +405,8 @@ __device__ void block_popc_prefix(const uint32_t* bm, PreT* pre, int W, unsigned
 // Numeric pass, one row: prefixes, owner-computes accumulation, fused scaling and beta D,
 // and the ordered write.  acc/wk share the accumulator region; bm holds the row bitmap.
 template <typename PreT>
-__device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, bool upper, int i,
-                            int W, int b, int64_t o0, int cnt, double* acc, unsigned* wk, const uint32_t* bm,
+__device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, bool upper, bool fz,
+                            int i, int W, int b, int64_t o0, int cnt, double* acc, unsigned* wk, const uint32_t* bm,
                             PreT* pre, int32_t* ci_out, double* v_out, double* row_sq, double* row_diag,
                             unsigned* ured, double* dred, unsigned long long* work_total) {
   const int nwarps = blockDim.x >> 5;
@@ -433,7 +435,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
     __syncthreads();  // every warp has read wk: the region now becomes the accumulator
     for (int k = threadIdx.x; k < cnt; k += T) acc[k] = 0.0;
     __syncthreads();
-    if (wa < wb) {
+    if (wa < wb && !fz) {
       const int c_lo = upper ? max(b + 32 * wa, i) : b + 32 * wa;
       const int c_hi = b + 32 * wb - 1;
       const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
@@ -511,17 +513,19 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
     }
   }
   __syncthreads();
-  // 4. scaling (Taylor /i) and the fused beta D term (squaring +2T), in that order
+  // 4. scaling (Taylor /i) and the fused beta D term (squaring +2T), in that order;
+  //    a frozen row is a plain copy of D
   if (div != 1.0)
     for (int k = threadIdx.x; k < cnt; k += T) acc[k] = acc[k] / div;
   __syncthreads();
   if (hasD) {
+    const double coef = fz ? 1.0 : beta;
     const int64_t d0 = D.rp[i], d1 = D.rp[i + 1];
     for (int64_t q = d0 + threadIdx.x; q < d1; q += T) {
       const int c = D.ci[q];
       if (upper && c < i) continue;
       const int pos = (int)rank_of(bm, pre, c - b);
-      acc[pos] += beta * D.v[q];
+      acc[pos] += coef * D.v[q];
     }
   }
   __syncthreads();
@@ -550,7 +554,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
 // prefixes (16- or 32-bit).
 template <bool GLOBAL>
 __global__ void k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, double beta, bool upper,
-                          const int32_t* rows,
+                          const uint8_t* frozen, const int32_t* rows,
                           int64_t nrows, const int32_t* base, const int32_t* words, const int64_t* rp_out,
                           int32_t* ci_out, double* v_out, double* row_sq, double* row_diag, unsigned char* gscratch,
                           int64_t gstride, unsigned long long* work_total) {
@@ -576,13 +580,14 @@ __global__ void k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, 
     if (row_diag && threadIdx.x == 0) row_diag[i] = 0.0;
     __syncthreads();
     // 1. pattern bitmap and products per word, from the word patterns
-    build_row_bitmap(A, WB, WD, hasD, i, b >> 5, bm, wk, upper);
+    const bool fz = frozen && frozen[i];
+    build_row_bitmap(A, WB, WD, hasD, i, b >> 5, bm, wk, upper, fz);
     __syncthreads();
     if (small_prefix(cnt))
-      numeric_row(A, B, D, div, beta, upper, i, W, b, o0, cnt, acc, wk, bm,
+      numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, acc, wk, bm,
                   reinterpret_cast<unsigned short*>(bm + W), ci_out, v_out, row_sq, row_diag, ured, dred, work_total);
     else
-      numeric_row(A, B, D, div, beta, upper, i, W, b, o0, cnt, acc, wk, bm, reinterpret_cast<unsigned*>(bm + W),
+      numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, acc, wk, bm, reinterpret_cast<unsigned*>(bm + W),
                   ci_out, v_out, row_sq, row_diag, ured, dred, work_total);
   }
 }
@@ -703,7 +708,8 @@ void word_pattern(const CsrD& X, cudaStream_t s, WPatOwned& out, HostScalars& hs
 }  // namespace
 
 int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, cudaStream_t s, CsrOwned& C,
-               RowStats* stats, HostScalars& hs, SpgemmTimes* times, bool upper, int64_t* done) {
+               RowStats* stats, HostScalars& hs, SpgemmTimes* times, bool upper, int64_t* done,
+               const uint8_t* frozen) {
   const int64_t n = A.n;
   EventPair ev_sym(times != nullptr, s), ev_num(times != nullptr, s);
   set_smem_limits();
@@ -734,7 +740,7 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
   {
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((n + 7) / 8, (int64_t)sms * 64);
-    k_analysis<<<(unsigned)blocks, threads, 0, s>>>(A, B, D, base.p, words.p, flops.p);
+    k_analysis<<<(unsigned)blocks, threads, 0, s>>>(A, B, D, frozen, base.p, words.p, flops.p);
     SX_CUDA(cudaGetLastError());
     k_sum_i64<<<(unsigned)std::min<int64_t>((n + 255) / 256, sms * 8), 256, 0, s>>>(flops.p, n, ctr.p + 2 * kClasses + 2);
     k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, words.p, nullptr, 0, lists.p, n, ctr.p, ctr.p + kClasses);
@@ -758,14 +764,14 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
       if (c < kClasses - 1) {
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 32);
         const int bytes = (int)((need + 1023) & ~1023ll);
-        k_symbolic<false><<<(unsigned)grid, threads, bytes, s>>>(A, WB, WD, hasD, lists.p + c * n, nr, base.p,
-                                                               words.p, cnt.p, nullptr, 0);
+        k_symbolic<false><<<(unsigned)grid, threads, bytes, s>>>(A, WB, WD, hasD, frozen, lists.p + c * n, nr,
+                                                               base.p, words.p, cnt.p, nullptr, 0);
       } else {
         const int64_t stride = (need / 4 + 63) & ~63ll;
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
         gs.reset((size_t)(stride * grid), s);
-        k_symbolic<true><<<(unsigned)grid, threads, 0, s>>>(A, WB, WD, hasD, lists.p + c * n, nr, base.p, words.p,
-                                                          cnt.p, gs.p, stride);
+        k_symbolic<true><<<(unsigned)grid, threads, 0, s>>>(A, WB, WD, hasD, frozen, lists.p + c * n, nr, base.p,
+                                                          words.p, cnt.p, gs.p, stride);
       }
       SX_CUDA(cudaGetLastError());
       count_launches(1);
@@ -795,13 +801,14 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 32);
         const int bytes = (int)((need + 1023) & ~1023ll);
         k_numeric<false><<<(unsigned)grid, threads, bytes, s>>>(
-            A, B, D, WB, WD, div, beta, upper, lists.p + c * n, nr, base.p, words.p, C.rp.p, C.ci.p, C.v.p,
+            A, B, D, WB, WD, div, beta, upper, frozen, lists.p + c * n, nr, base.p, words.p, C.rp.p, C.ci.p, C.v.p,
             stats ? stats->sq.p : nullptr, stats ? stats->diag.p : nullptr, nullptr, 0, ctr.p + 2 * kClasses + 3);
       } else {
         const int64_t stride = (need + 255) & ~255ll;
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
         gs.reset((size_t)(stride * grid), s);
-        k_numeric<true><<<(unsigned)grid, threads, 0, s>>>(A, B, D, WB, WD, div, beta, upper, lists.p + c * n, nr, base.p,
+        k_numeric<true><<<(unsigned)grid, threads, 0, s>>>(A, B, D, WB, WD, div, beta, upper, frozen, lists.p + c * n,
+                                                         nr, base.p,
                                                          words.p, C.rp.p, C.ci.p, C.v.p, stats ? stats->sq.p : nullptr,
                                                          stats ? stats->diag.p : nullptr, gs.p, stride,
                                                          ctr.p + 2 * kClasses + 3);

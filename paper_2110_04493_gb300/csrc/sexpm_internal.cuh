@@ -121,9 +121,11 @@ struct SpgemmTimes {
 // upper: A, B and D are symmetric (so is C); only the products at columns >= row are
 // formed and the entries below the diagonal are copied from their mirror entries.
 // done (optional) receives the number of products actually formed.
+// frozen (optional, one byte per row): rows with frozen[i] != 0 form no products and are a plain
+// copy of D_i (used by the batched method for instances that have finished their squarings).
 int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, cudaStream_t s,
                CsrOwned& C, RowStats* stats, HostScalars& hs, SpgemmTimes* times = nullptr, bool upper = false,
-               int64_t* done = nullptr);
+               int64_t* done = nullptr, const uint8_t* frozen = nullptr);
 
 // sum_i x[i] over n doubles, deterministic order.  Synchronises and returns the sum.
 double reduce_sum(const double* x, int64_t n, cudaStream_t s, HostScalars& hs);
@@ -161,5 +163,21 @@ bool csr_equal(const CsrD& A, const CsrD& B, double sign, cudaStream_t s, HostSc
 
 // Validation on device: sorted unique in-range columns, finite values, monotone row_ptr.
 bool csr_valid(const CsrD& A, cudaStream_t s, HostScalars& hs);
+
+// ---------------------------------------------------------------- batched (block-diagonal) helpers
+// inst[i]: instance of row i; seg[b] .. seg[b+1]: rows of instance b (device arrays).
+
+// sums_host[b] = sum over instance b's rows of x (device x; synchronises s).
+void seg_sums(const double* x, const int64_t* seg, int count, double* out_host, cudaStream_t s);
+// Algorithm 4.1 pass with thresholds t_inst[b] (device): keep[i] and per-instance sums.
+void filter_pass_seg(const CsrD& A, const int32_t* inst, const double* t_inst, int32_t* keep, double* row_part,
+                     const int64_t* seg, int count, double* sums_host, cudaStream_t s);
+void compact_seg(const CsrD& A, const int32_t* inst, const double* t_inst, CsrOwned& C, cudaStream_t s);
+void scale_rows(const CsrD& A, const int32_t* inst, const double* factor, double* out_v, cudaStream_t s);
+void instance_of_row(const int64_t* seg, int count, int64_t n, int32_t* inst, cudaStream_t s);
+void row_flags(const int32_t* inst, const uint8_t* inst_flag, int64_t n, uint8_t* row_flag, cudaStream_t s);
+void block_put(const CsrD& X, int64_t row0, int64_t nnz0, int64_t* rp, int32_t* ci, double* v, cudaStream_t s);
+void block_get(const CsrD& E, int64_t row0, int64_t nb, int64_t nnz_b, CsrOwned& out, cudaStream_t s);
+void gather_row_ptr(const int64_t* rp, const int64_t* seg, int count, int64_t* out_host, cudaStream_t s);
 
 }  // namespace sexpm

@@ -93,6 +93,8 @@ def load() -> ctypes.CDLL:
                                P(ctypes.c_int64)]
     L.sexpm_filter.argtypes = [P(CsrView), ctypes.c_double, ctypes.c_double, ctypes.c_int32, vp, P(vp),
                                P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_double)]
+    L.sexpm_plan_batched.argtypes = [P(CsrView), ctypes.c_int32, ctypes.c_double, P(Options), vp, P(vp)]
+    L.sexpm_compute_batched.argtypes = [vp, P(ctypes.c_double), P(vp)]
     L.sexpm_filter_noalloc.argtypes = [P(CsrView), ctypes.c_double, ctypes.c_double, ctypes.c_int32, vp, vp, vp, vp,
                                        ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_int32),
                                        P(ctypes.c_double)]
@@ -262,6 +264,53 @@ def expm(H, tau: float = 1.0, eps: float = 1e-12, device="cuda", **opts):
     finally:
         plan.close()
     return out, st
+
+
+class BatchedPlan:
+    """sexpm_plan_batched: many matrices planned as one block-diagonal problem."""
+
+    def __init__(self, Hs, eps: float, stream=None, **opts):
+        keep: List[Any] = []
+        views = (CsrView * len(Hs))(*[_make_view(H, keep) for H in Hs])
+        self.count = len(Hs)
+        self._stream = _stream_ptr(stream)
+        h = ctypes.c_void_p()
+        o = options(**opts)
+        _check(load().sexpm_plan_batched(views, self.count, float(eps), ctypes.byref(o), self._stream,
+                                         ctypes.byref(h)))
+        self._h = h
+
+    def compute(self, taus) -> List[Result]:
+        taus = (ctypes.c_double * self.count)(*[float(t) for t in taus])
+        outs = (ctypes.c_void_p * self.count)()
+        _check(load().sexpm_compute_batched(self._h, taus, outs))
+        return [Result(outs[k]) for k in range(self.count)]
+
+    def close(self) -> None:
+        if self._h:
+            load().sexpm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def expm_batched(Hs, taus, eps: float = 1e-12, device="cuda", **opts):
+    """[e^{tau_b H_b}] as a list of ((row_ptr, col, val), stats) through the batched entry points."""
+    plan = BatchedPlan(Hs, eps, **opts)
+    try:
+        out = []
+        for r in plan.compute(taus):
+            try:
+                out.append((r.to_torch(device), r.stats()))
+            finally:
+                r.free()
+    finally:
+        plan.close()
+    return out
 
 
 def spgemm(A, B, D=None, div: float = 1.0, beta: float = 0.0, device="cuda"):

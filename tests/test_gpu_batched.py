@@ -1,0 +1,89 @@
+"""Batched form: many independent e^{tau_b H_b} in one block-diagonal run (sexpm_plan_batched /
+sexpm_compute_batched), each instance held to the same parity bar against the oracle as the
+plain path."""
+import numpy as np
+import pytest
+
+from oracle import sexpm_oracle as O
+from tests._compare import expm_parity, to_scipy, torch_csr
+from workloads import CSR, diag_scale, dirichlet_laplacian, laplacian_batch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sx():
+    from paper_2110_04493_gb300 import build as B
+    B.build()
+    from paper_2110_04493_gb300 import sexpm
+    sexpm.load()
+    return sexpm
+
+
+def _check_batch(sx, items, eps, **opts):
+    outs = sx.expm_batched([torch_csr(H) for H, _ in items], [t for _, t in items], eps, **opts)
+    assert len(outs) == len(items)
+    for (H, tau), ((rp, ci, v), st) in zip(items, outs):
+        G = to_scipy(rp, ci, v, H.n)
+        E, so = O.expm(H.to_scipy(), tau, eps)
+        assert (st["M"], st["N"]) == (so.M, so.N)
+        assert bool(st["normal"]) == bool(so.normal)
+        ts = [r["t"] for r in st["steps"]] + [s.t for s in so.steps] + [t.t for t in so.taylor]
+        expm_parity(G, E, max(ts) if ts else 0.0)
+    return outs
+
+
+@pytest.mark.parametrize("symmetric", [1, 0])
+def test_batched_laplacians_match_oracle(sx, symmetric):
+    """Twelve 2-D Laplacians of different sizes and tau (different M_b, N_b)."""
+    items = laplacian_batch(count=12, seed=5, side_lo=4, side_hi=24, tau_lo=1e-4, tau_hi=1e-2)
+    outs = _check_batch(sx, items, 1e-12, symmetric=symmetric)
+    assert len({st["N"] for _, st in outs}) > 1  # the instances really need different step counts
+
+
+def test_batched_mixed_instances(sx):
+    """Non-symmetric, scalar, zero and ragged instances in one batch."""
+    L = dirichlet_laplacian(6, 3)
+    DL, _ = diag_scale(L, seed=4)
+    Z = CSR(4, np.array([0, 1, 1, 1, 1], dtype=np.int64), np.array([2], dtype=np.int32), np.zeros(1))
+    items = [(DL, 2.0 / 49.0), (CSR.from_dense([[-2.0]]), 0.3), (Z, 1.0), (dirichlet_laplacian(9, 2), 1e-3),
+             (CSR.from_dense([[1.0, 1e3], [0.0, 0.5]]), 1.0)]
+    _check_batch(sx, items, 1e-12)
+
+
+def test_batched_single_instance_equals_plain(sx):
+    H = dirichlet_laplacian(20, 2)
+    tau = 2e-3
+    [((rp, ci, v), st)] = sx.expm_batched([torch_csr(H)], [tau], 1e-12)
+    (rp2, ci2, v2), st2 = sx.expm(torch_csr(H), tau, 1e-12)
+    A, B = to_scipy(rp, ci, v, H.n), to_scipy(rp2, ci2, v2, H.n)
+    assert (st["M"], st["N"]) == (st2["M"], st2["N"])
+    assert abs(A - B).max() <= 1e-14
+
+
+def _sine_basis_expm(m, tau):
+    h = 1.0 / (m + 1)
+    j = np.arange(1, m + 1)
+    lam = -(4.0 / h ** 2) * np.sin(j * np.pi * h / 2) ** 2
+    V = np.sqrt(2 * h) * np.sin(np.outer(j, j) * np.pi * h)
+    return (V * np.exp(tau * lam)) @ V.T
+
+
+def test_batched_full_workload_against_closed_form(sx):
+    """The 256-instance workload (sides 16..128, tau log-uniform in [1e-4, 1e-2], eps = 1e-12),
+    run as one batch exactly as bench.py times it; every instance is checked on sampled entries
+    against e^{tau L_1} (x) e^{tau L_1} built from the 1-D sine eigenbasis."""
+    from workloads import BATCH_EPS
+    items = laplacian_batch()
+    outs = sx.expm_batched([torch_csr(H) for H, _ in items], [t for _, t in items], BATCH_EPS)
+    rng = np.random.default_rng(0)
+    for (H, tau), ((rp, ci, v), st) in zip(items, outs):
+        m = int(round(np.sqrt(H.n)))
+        E1 = _sine_basis_expm(m, tau)
+        G = to_scipy(rp, ci, v, H.n)
+        rows = rng.integers(0, H.n, size=8)
+        for i in rows:
+            row = G.getrow(int(i)).toarray().ravel()
+            xi, yi = i % m, i // m
+            exact = np.outer(E1[yi], E1[xi]).ravel()  # node j = x + m y
+            assert np.abs(row - exact).max() <= 1e-11, (H.n, tau, i)

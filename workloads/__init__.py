@@ -5,6 +5,7 @@ matrix-exponential method's arithmetic, so the CUDA path and the CPU oracle
 can both draw their inputs from it without sharing any computation.
 """
 from .generators import (  # noqa: F401
+    BATCH_EPS,
     CSR,
     CONFIGS,
     Config,
@@ -13,6 +14,7 @@ from .generators import (  # noqa: F401
     diag_weights,
     dirichlet_laplacian,
     get_config,
+    laplacian_batch,
     paper_table1_matrices,
     random_csr,
     rgg_adjacency,

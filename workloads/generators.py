@@ -196,6 +196,17 @@ CONFIGS: Dict[str, Config] = {
 }
 
 
+def laplacian_batch(count: int = 256, seed: int = 2, side_lo: int = 16, side_hi: int = 128,
+                    tau_lo: float = 1e-4, tau_hi: float = 1e-2) -> List[Tuple[CSR, float]]:
+    """Independent 2-D Dirichlet Laplacians (h = 1/(side+1)) with their own tau: the batched
+    workload (256 instances, side ~ U{16..128}, tau log-uniform in [1e-4, 1e-2], seed 2)."""
+    return [(dirichlet_laplacian(side, 2), tau)
+            for side, tau in batch_instances(count, seed, side_lo, side_hi, tau_lo, tau_hi)]
+
+
+BATCH_EPS = 1e-12
+
+
 def get_config(name: str, scale_m: int = 0) -> Config:
     """Named workload; scale_m > 0 gives the same grid family on an m = scale_m grid with the
     same tau/h^2 (so the same per-row kernel width) and tolerance."""
