@@ -339,3 +339,74 @@ def bandwidth(A: sp.csr_matrix) -> int:
         return 0
     d = A.col[nz].astype(np.int64) - A.row[nz].astype(np.int64)
     return int(max(d.max(), 0) + max((-d).max(), 0))
+
+
+# --------------------------------------------------------------------------
+# Adjoint of the filtered method (masks frozen)
+# --------------------------------------------------------------------------
+#
+# With the scaling N, the Taylor degree and every filter decision held fixed (they are
+# piecewise constant in H), Algorithm 4.2 is a polynomial map H -> e^H:
+#   S_1 = H_0,  S_i = P_i(S_{i-1} H_0 / i),  T_0 = sum_i S_i,
+#   T_k = Q_k(2 T_{k-1} + T_{k-1}^2),  E = I + T_N,      H_0 = tau 2^-N H,
+# where P_i, Q_k keep the stored pattern of the filtered S^_i, T^_k.  For L = <W, E> its
+# reverse pass is, with Y = dL/dT_k on the pattern of T_k,
+#   dL/dT_{k-1} = mask_{k-1}(2 Y + Y T_{k-1}^T + T_{k-1}^T Y)            (from Eq. (4.15)),
+# then dL/dS_i = dL/dT_0 on the pattern of S_i, and for i = M'..2
+#   dL/dS_{i-1} += mask(Y H_0^T) / i,   dL/dH_0 += mask_H(S_{i-1}^T Y) / i   (Y = dL/dS_i),
+#   dL/dH_0 += dL/dS_1,  dL/dH = tau 2^-N dL/dH_0   (on the pattern of H).
+
+def _ones(P: sp.csr_matrix) -> sp.csr_matrix:
+    P = _canon(P)
+    return sp.csr_matrix((np.ones(P.nnz), P.indices, P.indptr), shape=P.shape)
+
+
+def restrict(X, P) -> sp.csr_matrix:
+    """X on the stored pattern of P (entries of P's pattern missing from X are zeros)."""
+    out = _canon(sp.csr_matrix(X).multiply(_ones(P)))
+    return out
+
+
+def square_adjoint(Y, Tp) -> sp.csr_matrix:
+    """dL/dT_{k-1} = mask_{k-1}(2 Y + Y T_{k-1}^T + T_{k-1}^T Y) for T_k = Q_k(2 T_{k-1} + T_{k-1}^2)."""
+    return restrict(2.0 * Y + Y @ Tp.T + Tp.T @ Y, Tp)
+
+
+def adjoint(H, tau: float, eps_tol: float, W, e_r: float = 0.1, square_scale: str = "rel",
+            normal: Optional[bool] = None, max_iter: int = 100):
+    """dL/dH on the pattern of H for L = <W, e^{tau H}> (W sparse), masks frozen.
+
+    Returns (G as scipy CSR with the pattern of H, E, stats, trace)."""
+    H = _canon(H)
+    E, st, tr = expm(H, tau, eps_tol, e_r, square_scale, normal, max_iter, keep=True)
+    if st.M == 0:
+        return restrict(sp.csr_matrix(H.shape), H), E, st, tr
+    H0, S, T = tr["H0"], tr["S"], tr["T"]
+    G = restrict(W, T[-1])
+    for k in range(len(T) - 1, 0, -1):
+        G = square_adjoint(G, T[k - 1])
+    GS = [restrict(G, Si) for Si in S]
+    GH0 = restrict(sp.csr_matrix(H.shape), H)
+    for i in range(len(S), 1, -1):
+        Y = GS[i - 1]
+        GS[i - 2] = _canon(GS[i - 2] + restrict(Y @ H0.T, S[i - 2]) / i)
+        GH0 = _canon(GH0 + restrict(S[i - 2].T @ Y, H) / i)
+    GH0 = _canon(GH0 + restrict(GS[0], H))
+    GH = GH0 * (tau * math.ldexp(1.0, -st.N))
+    return restrict(GH, H), E, st, tr
+
+
+def forward_frozen(H, tau: float, N: int, S_masks, T_masks) -> sp.csr_matrix:
+    """Algorithm 4.2 with N and every filter decision given: e^{tau H} as the polynomial map
+    that the adjoint differentiates (S_masks[i-1] the pattern of S^_i, T_masks[k] of T^_k)."""
+    H = _canon(H)
+    H0 = H * (tau * math.ldexp(1.0, -N))
+    S = restrict(H0, S_masks[0])
+    T = S.copy()
+    for i in range(2, len(S_masks) + 1):
+        S = restrict(S @ H0 / i, S_masks[i - 1])
+        T = _canon(T + S)
+    T = restrict(T, T_masks[0])
+    for k in range(1, len(T_masks)):
+        T = restrict(2.0 * T + T @ T, T_masks[k])
+    return _canon(sp.identity(H.shape[0], format="csr") + T)
