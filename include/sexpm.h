@@ -191,6 +191,23 @@ int sexpm_plan_batched(const sexpm_csr_view* Hs, int32_t count, double eps, cons
  * is sexpm_compute with taus[0]. */
 int sexpm_compute_batched(sexpm_plan_t* plan, const double* taus, sexpm_result_t** outs);
 
+/* ---------------------------------------------------------- adjoint form */
+
+/* Gradient of a scalar loss through e^{tau H}: given W = dL/dE for E = e^{tau H} (a sparse
+ * matrix; only its entries on the pattern of E matter), returns dL/dH on the stored pattern
+ * of H.  The derivative is that of the map the method computes with the scaling N, the Taylor
+ * degree and every filter decision (the kept patterns of Algorithm 4.1) held fixed, which is
+ * piecewise constant in H: with Y = dL/dT^_k on the pattern of T^_k,
+ *   dL/dT^_{k-1} = mask_{k-1}(2 Y + Y T^_{k-1}^T + T^_{k-1}^T Y)     (reverse of Eq. 4.15),
+ * then the reverse of the Taylor recursion of Eq. (4.11), and dL/dH = tau 2^-N dL/dH_0.
+ * The forward pass is rerun with every product formed; T^_k is kept every ckpt_stride
+ * squarings (0: ceil(sqrt(N))) and the iterates in between are recomputed in the reverse pass.
+ * *dH receives a result with the pattern of H (its stats are those of the forward run);
+ * if expm_out is not NULL it receives e^{tau H} of that forward run.  Not in the paper
+ * (the benchmark spec's differentiation form). */
+int sexpm_adjoint(sexpm_plan_t* plan, double tau, const sexpm_csr_view* W, int32_t ckpt_stride,
+                  sexpm_result_t** dH, sexpm_result_t** expm_out);
+
 /* ------------------------------------------------------------ step calls */
 /* The individual steps of the hot path on caller-provided device CSR views,
  * for testing and measurement.  Outputs are new result handles. */

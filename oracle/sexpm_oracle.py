@@ -380,7 +380,8 @@ def adjoint(H, tau: float, eps_tol: float, W, e_r: float = 0.1, square_scale: st
     H = _canon(H)
     E, st, tr = expm(H, tau, eps_tol, e_r, square_scale, normal, max_iter, keep=True)
     if st.M == 0:
-        return restrict(sp.csr_matrix(H.shape), H), E, st, tr
+        # ||tau H|| = 0: e^{tau H} = I + tau H + ..., so dL/dH = tau W on the pattern of H
+        return restrict(sp.csr_matrix(W) * tau, H), E, st, tr
     H0, S, T = tr["H0"], tr["S"], tr["T"]
     G = restrict(W, T[-1])
     for k in range(len(T) - 1, 0, -1):

@@ -8,9 +8,11 @@ from .sexpm import (  # noqa: F401
     BatchedPlan,
     Plan,
     Result,
+    adjoint,
     SexpmError,
     choose_MN,
     expm,
+    expm_autograd,
     expm_batched,
     filter_csr,
     load,

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -321,6 +322,226 @@ struct sexpm_result {
   std::vector<sexpm_step_stats> steps;
 };
 
+// ---------------------------------------------------------------- the method (Algorithm 4.2)
+
+// What the reverse pass needs from a forward run: H_0, the kept Taylor terms S_1..S_M'
+// (S_1 = H_0), and T^_k at the checkpoints k = 0, stride, 2 stride, ..., N, together with the
+// scalars that let a squaring step be replayed bit for bit.
+struct Record {
+  int stride = 0;  // 0: ceil(sqrt(N))
+  CsrOwned H0;
+  std::vector<CsrOwned> S;
+  std::map<int, CsrOwned> T;
+  int M = 0, N = 0;
+  double tau = 0.0, a = 0.0, r0 = 0.0;
+};
+
+// One filtered incremental squaring T^_k = filter(2 T^_{k-1} + T^_{k-1}^2) (Eq. 4.15 with the
+// threshold of reading 8); deterministic, so a replay reproduces the forward exactly.
+void square_step(const sexpm_options& o, const CsrD& T, int k, double a, double r0, bool sym, cudaStream_t s,
+                 HostScalars& hs, RowStats& rs, CsrOwned& Tn, sexpm_step_stats* rec) {
+  Timer ts(s);
+  const int64_t n = T.n;
+  const double ri = std::ldexp(r0, k);
+  CsrOwned Tt;
+  SpgemmTimes tm;
+  int64_t done = 0;
+  const int64_t prod = spgemm(T, T, T, 1.0, 2.0, s, Tt, &rs, hs, &tm, sym, &done);
+  const double flops = 2.0 * (double)done + 2.0 * (double)T.nnz;
+  double normF = 1.0;
+  if (o.square_scale) {
+    const double sq = reduce_sum(rs.sq.p, n, s, hs);
+    const double tr = reduce_sum(rs.diag.p, n, s, hs);
+    const double f2 = sq + (double)n + 2.0 * tr;
+    normF = std::sqrt(f2 > 0.0 ? f2 : 0.0);
+  }
+  const double eps_g = a * ri * normF;
+  FilterOut fo = filter_alg41(Tt.view(), eps_g, o.e_r, o.max_filter_iters, s, Tn, hs);
+  if (rec) {
+    std::memset(rec, 0, sizeof(*rec));
+    rec->phase = 1;
+    rec->i = k;
+    rec->iters = fo.iters;
+    rec->eps_g = eps_g;
+    rec->t = fo.t;
+    rec->b = fo.b;
+    rec->norm_F = o.square_scale ? normF : 0.0;
+    rec->nnz_raw = Tt.nnz;
+    rec->nnz = Tn.nnz;
+    rec->products = prod;
+    rec->products_done = done;
+    rec->ms_symbolic = tm.ms_symbolic;
+    rec->ms_numeric = tm.ms_numeric;
+    rec->ms_filter = fo.ms;
+    rec->flops = flops;
+    rec->bytes_filter = fo.bytes;
+    rec->ms = ts.ms();
+  }
+}
+
+void compute_impl(sexpm_plan_t* p, double tau, sexpm_result* res, Record* record, bool allow_sym) {
+  if (!std::isfinite(tau)) fail(SEXPM_EINVAL, "tau must be finite");
+  int dev = 0;
+  SX_CUDA(cudaGetDevice(&dev));
+  if (dev != p->device) fail(SEXPM_EINVAL, "current device differs from the plan's device");
+  cudaStream_t s = p->s;
+  HostScalars& hs = p->hs;
+  const sexpm_options& o = p->opt;
+  const int64_t n = p->H.n;
+  res->s = s;
+  std::memset(&res->st, 0, sizeof(res->st));
+  sexpm_stats_t& st = res->st;
+  st.n = n;
+  Pool::reset_peak();
+  const int64_t live0 = Pool::live();
+  const int64_t launches0 = launches();
+  Timer t_all(s);
+  // step 1: tau H and its F-norm, (M, N)
+  CsrD Hs = p->H.view();
+  DevBuf<double> hv(p->H.nnz, s);
+  scale_values(p->H.v.p, tau, p->H.nnz, hv.p, s);
+  Hs.v = hv.p;
+  const double normH = std::sqrt(sum_squares(Hs, s, hs));
+  st.norm_H = normH;
+  int32_t M = 0, N = 0;
+  const int rc = sexpm_choose_MN(normH, p->eps, o.n_extra, o.max_taylor, &M, &N);
+  if (rc != SEXPM_OK) fail(rc, rc == SEXPM_ENOPARAM ? "no feasible (M, N) for this tolerance" : "invalid (M, N) input");
+  st.M = M;
+  st.N = N;
+  const bool normal = (p->normal != 0) || normH == 0.0;
+  st.normal = normal ? 1 : 0;
+  const bool sym = p->symmetric && allow_sym;
+  st.symmetric = sym ? 1 : 0;
+  if (record) {
+    record->M = M;
+    record->N = N;
+    record->tau = tau;
+    if (record->stride <= 0) record->stride = std::max(1, (int)std::ceil(std::sqrt((double)N)));
+  }
+  if (M == 0) {
+    // ||tau H|| = 0: e^0 = I
+    CsrOwned Z;
+    Z.n = n;
+    Z.nnz = 0;
+    Z.rp.reset(n + 1, s);
+    SX_CUDA(cudaMemsetAsync(Z.rp.p, 0, (n + 1) * sizeof(int64_t), s));
+    add_identity(Z.view(), s, res->E, hs);
+    st.nnz_out = res->E.nnz;
+    st.ms_total = t_all.ms();
+    st.peak_bytes = Pool::peak() - live0;
+    st.launches = launches() - launches0;
+    return;
+  }
+  // step 2: filter parameter a
+  const double a = normal ? 1.0 / (1.0 + N) : 1.0 / normH;
+  st.a = a;
+  // step 3: Taylor phase on H_0 = tau H 2^-N
+  Timer t_tay(s);
+  DevBuf<double> h0v(p->H.nnz, s);
+  scale_values(hv.p, std::ldexp(1.0, -N), p->H.nnz, h0v.p, s);
+  CsrD H0 = Hs;
+  H0.v = h0v.p;
+  const double x0 = std::ldexp(normH, -N);
+  const double r0 = sexpm_rho(M, x0);
+  const double eps_g0 = a * r0 / ((double)M * std::exp(2.0 * x0));
+  st.r0 = r0;
+  st.eps_g0 = eps_g0;
+  if (record) {
+    record->a = a;
+    record->r0 = r0;
+    copy_csr(H0, s, record->H0);
+    record->S.emplace_back();
+    copy_csr(H0, s, record->S.back());
+  }
+  CsrOwned T;       // running T^_0, later T^_i
+  copy_csr(H0, s, T);
+  CsrOwned S;       // current filtered term (S_1 = H_0 is not filtered)
+  CsrD Sv = H0;
+  CsrD none;
+  for (int i = 2; i <= M; ++i) {
+    Timer ts(s);
+    CsrOwned St;
+    SpgemmTimes tm;
+    int64_t done = 0;
+    const int64_t prod = spgemm(Sv, H0, none, (double)i, 0.0, s, St, nullptr, hs, &tm, false, &done);
+    CsrOwned Sn;
+    FilterOut fo = filter_alg41(St.view(), eps_g0, o.e_r, o.max_filter_iters, s, Sn, hs);
+    sexpm_step_stats rec;
+    std::memset(&rec, 0, sizeof(rec));
+    rec.phase = 0;
+    rec.i = i;
+    rec.iters = fo.iters;
+    rec.eps_g = eps_g0;
+    rec.t = fo.t;
+    rec.b = fo.b;
+    rec.nnz_raw = St.nnz;
+    rec.nnz = Sn.nnz;
+    rec.products = prod;
+    rec.ms_symbolic = tm.ms_symbolic;
+    rec.ms_numeric = tm.ms_numeric;
+    rec.ms_filter = fo.ms;
+    rec.products_done = done;
+    rec.flops = 2.0 * (double)done + (double)St.nnz;
+    rec.bytes_filter = fo.bytes;
+    if (Sn.nnz == 0) {
+      rec.ms = ts.ms();
+      res->steps.push_back(rec);
+      break;
+    }
+    if (record) {
+      record->S.emplace_back();
+      copy_csr(Sn.view(), s, record->S.back());
+    }
+    CsrOwned Tn;
+    add(T.view(), Sn.view(), 1.0, s, Tn, hs);
+    T = std::move(Tn);
+    S = std::move(Sn);
+    Sv = S.view();
+    rec.ms = ts.ms();
+    res->steps.push_back(rec);
+  }
+  S.rp.free(); S.ci.free(); S.v.free();
+  if (sym) {
+    // For symmetric H the exact T_0 is symmetric, but a filtered term S^_i no longer commutes
+    // with H_0, so S^_{i-1} H_0 (and T^_0) can lose symmetry at the level of the dropped
+    // entries.  T^_0 <- (T^_0 + T^_0^T)/2 restores it; from then on every T~_i = 2T + T T is
+    // symmetric and the squarings form only the entries at columns >= row.
+    CsrOwned Ts;
+    symmetric_part(T.view(), s, Ts, hs);
+    T = std::move(Ts);
+  }
+  if (record) copy_csr(T.view(), s, record->T[0]);
+  st.ms_taylor = t_tay.ms();
+  // step 4: N filtered squarings
+  Timer t_sq(s);
+  RowStats rs;
+  for (int i = 1; i <= N; ++i) {
+    CsrOwned Tn;
+    sexpm_step_stats rec;
+    square_step(o, T.view(), i, a, r0, sym, s, hs, rs, Tn, &rec);
+    T = std::move(Tn);
+    res->steps.push_back(rec);
+    if (record && (i % record->stride == 0 || i == N)) copy_csr(T.view(), s, record->T[i]);
+  }
+  st.ms_squaring = t_sq.ms();
+  // step 5: e^{tau H} = I + T^_N
+  Timer t_fin(s);
+  add_identity(T.view(), s, res->E, hs);
+  st.ms_final = t_fin.ms();
+  st.nnz_out = res->E.nnz;
+  st.n_steps = (int32_t)res->steps.size();
+  st.ms_total = t_all.ms();
+  st.peak_bytes = Pool::peak() - live0;
+  st.launches = launches() - launches0;
+}
+
+// A device CSR with the pattern of P and the values v (non-owning).
+CsrD with_values(const CsrD& P, const double* v) {
+  CsrD d = P;
+  d.v = v;
+  return d;
+}
+
 #define SX_API_BEGIN try {
 #define SX_API_END                                         \
   }                                                        \
@@ -401,180 +622,10 @@ int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
   SX_API_BEGIN
   if (!p || !out) fail(SEXPM_EINVAL, "null argument");
   *out = nullptr;
-  if (!std::isfinite(tau)) fail(SEXPM_EINVAL, "tau must be finite");
   if (p->count > 0) fail(SEXPM_EINVAL, "batched plan: use sexpm_compute_batched");
-  int dev = 0;
-  SX_CUDA(cudaGetDevice(&dev));
-  if (dev != p->device) fail(SEXPM_EINVAL, "current device differs from the plan's device");
-  cudaStream_t s = p->s;
-  HostScalars& hs = p->hs;
-  const sexpm_options& o = p->opt;
-  const int64_t n = p->H.n;
   sexpm_result* res = new sexpm_result();
   try {
-    res->s = s;
-    std::memset(&res->st, 0, sizeof(res->st));
-    sexpm_stats_t& st = res->st;
-    st.n = n;
-    Pool::reset_peak();
-    const int64_t live0 = Pool::live();
-    const int64_t launches0 = launches();
-    Timer t_all(s);
-    // step 1: tau H and its F-norm, (M, N)
-    CsrD Hs = p->H.view();
-    DevBuf<double> hv(p->H.nnz, s);
-    scale_values(p->H.v.p, tau, p->H.nnz, hv.p, s);
-    Hs.v = hv.p;
-    const double normH = std::sqrt(sum_squares(Hs, s, hs));
-    st.norm_H = normH;
-    int32_t M = 0, N = 0;
-    const int rc = sexpm_choose_MN(normH, p->eps, o.n_extra, o.max_taylor, &M, &N);
-    if (rc != SEXPM_OK) fail(rc, rc == SEXPM_ENOPARAM ? "no feasible (M, N) for this tolerance" : "invalid (M, N) input");
-    st.M = M;
-    st.N = N;
-    const bool normal = (p->normal != 0) || normH == 0.0;
-    st.normal = normal ? 1 : 0;
-    const bool sym = p->symmetric && o.symmetric;
-    st.symmetric = sym ? 1 : 0;
-    if (M == 0) {
-      // ||tau H|| = 0: e^0 = I
-      CsrOwned Z;
-      Z.n = n;
-      Z.nnz = 0;
-      Z.rp.reset(n + 1, s);
-      SX_CUDA(cudaMemsetAsync(Z.rp.p, 0, (n + 1) * sizeof(int64_t), s));
-      add_identity(Z.view(), s, res->E, hs);
-      st.nnz_out = res->E.nnz;
-      st.ms_total = t_all.ms();
-      st.peak_bytes = Pool::peak() - live0;
-      st.launches = launches() - launches0;
-      *out = res;
-      set_last_error("");
-      return SEXPM_OK;
-    }
-    // step 2: filter parameter a
-    const double a = normal ? 1.0 / (1.0 + N) : 1.0 / normH;
-    st.a = a;
-    // step 3: Taylor phase on H_0 = tau H 2^-N
-    Timer t_tay(s);
-    DevBuf<double> h0v(p->H.nnz, s);
-    scale_values(hv.p, std::ldexp(1.0, -N), p->H.nnz, h0v.p, s);
-    CsrD H0 = Hs;
-    H0.v = h0v.p;
-    const double x0 = std::ldexp(normH, -N);
-    const double r0 = sexpm_rho(M, x0);
-    const double eps_g0 = a * r0 / ((double)M * std::exp(2.0 * x0));
-    st.r0 = r0;
-    st.eps_g0 = eps_g0;
-    CsrOwned T;       // running T^_0, later T^_i
-    copy_csr(H0, s, T);
-    CsrOwned S;       // current filtered term (S_1 = H_0 is not filtered)
-    CsrD Sv = H0;
-    CsrD none;
-    for (int i = 2; i <= M; ++i) {
-      Timer ts(s);
-      CsrOwned St;
-      SpgemmTimes tm;
-      int64_t done = 0;
-      const int64_t prod = spgemm(Sv, H0, none, (double)i, 0.0, s, St, nullptr, hs, &tm, false, &done);
-      CsrOwned Sn;
-      FilterOut fo = filter_alg41(St.view(), eps_g0, o.e_r, o.max_filter_iters, s, Sn, hs);
-      sexpm_step_stats rec;
-      std::memset(&rec, 0, sizeof(rec));
-      rec.phase = 0;
-      rec.i = i;
-      rec.iters = fo.iters;
-      rec.eps_g = eps_g0;
-      rec.t = fo.t;
-      rec.b = fo.b;
-      rec.nnz_raw = St.nnz;
-      rec.nnz = Sn.nnz;
-      rec.products = prod;
-      rec.ms_symbolic = tm.ms_symbolic;
-      rec.ms_numeric = tm.ms_numeric;
-      rec.ms_filter = fo.ms;
-      rec.products_done = done;
-      rec.flops = 2.0 * (double)done + (double)St.nnz;
-      rec.bytes_filter = fo.bytes;
-      if (Sn.nnz == 0) {
-        rec.ms = ts.ms();
-        res->steps.push_back(rec);
-        break;
-      }
-      CsrOwned Tn;
-      add(T.view(), Sn.view(), 1.0, s, Tn, hs);
-      T = std::move(Tn);
-      S = std::move(Sn);
-      Sv = S.view();
-      rec.ms = ts.ms();
-      res->steps.push_back(rec);
-    }
-    S.rp.free(); S.ci.free(); S.v.free();
-    if (sym) {
-      // For symmetric H the exact T_0 is symmetric, but a filtered term S^_i no longer commutes
-      // with H_0, so S^_{i-1} H_0 (and T^_0) can lose symmetry at the level of the dropped
-      // entries.  T^_0 <- (T^_0 + T^_0^T)/2 restores it; from then on every T~_i = 2T + T T is
-      // symmetric and the squarings form only the entries at columns >= row.
-      CsrOwned Ts;
-      symmetric_part(T.view(), s, Ts, hs);
-      T = std::move(Ts);
-    }
-    st.ms_taylor = t_tay.ms();
-    // step 4: N filtered squarings
-    Timer t_sq(s);
-    RowStats rs;
-    for (int i = 1; i <= N; ++i) {
-      Timer ts(s);
-      const double ri = std::ldexp(r0, i);
-      CsrOwned Tt;
-      SpgemmTimes tm;
-      int64_t done = 0;
-      const int64_t prod = spgemm(T.view(), T.view(), T.view(), 1.0, 2.0, s, Tt, &rs, hs, &tm, sym, &done);
-      const double flops = 2.0 * (double)done + 2.0 * (double)T.nnz;
-      double normF = 1.0;
-      if (o.square_scale) {
-        const double sq = reduce_sum(rs.sq.p, n, s, hs);
-        const double tr = reduce_sum(rs.diag.p, n, s, hs);
-        const double f2 = sq + (double)n + 2.0 * tr;
-        normF = std::sqrt(f2 > 0.0 ? f2 : 0.0);
-      }
-      const double eps_g = a * ri * normF;
-      T.rp.free(); T.ci.free(); T.v.free();
-      CsrOwned Tn;
-      FilterOut fo = filter_alg41(Tt.view(), eps_g, o.e_r, o.max_filter_iters, s, Tn, hs);
-      sexpm_step_stats rec;
-      std::memset(&rec, 0, sizeof(rec));
-      rec.phase = 1;
-      rec.i = i;
-      rec.iters = fo.iters;
-      rec.eps_g = eps_g;
-      rec.t = fo.t;
-      rec.b = fo.b;
-      rec.norm_F = o.square_scale ? normF : 0.0;
-      rec.nnz_raw = Tt.nnz;
-      rec.nnz = Tn.nnz;
-      rec.products = prod;
-      rec.products_done = done;
-      rec.ms_symbolic = tm.ms_symbolic;
-      rec.ms_numeric = tm.ms_numeric;
-      rec.ms_filter = fo.ms;
-      rec.flops = flops;
-      rec.bytes_filter = fo.bytes;
-      Tt.rp.free(); Tt.ci.free(); Tt.v.free();
-      T = std::move(Tn);
-      rec.ms = ts.ms();
-      res->steps.push_back(rec);
-    }
-    st.ms_squaring = t_sq.ms();
-    // step 5: e^{tau H} = I + T^_N
-    Timer t_fin(s);
-    add_identity(T.view(), s, res->E, hs);
-    st.ms_final = t_fin.ms();
-    st.nnz_out = res->E.nnz;
-    st.n_steps = (int32_t)res->steps.size();
-    st.ms_total = t_all.ms();
-    st.peak_bytes = Pool::peak() - live0;
-    st.launches = launches() - launches0;
+    compute_impl(p, tau, res, nullptr, p->opt.symmetric != 0);
   } catch (...) {
     delete res;
     throw;
@@ -976,6 +1027,127 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
     throw;
   }
   for (int b = 0; b < count; ++b) outs[b] = res[b];
+  SX_API_END
+}
+
+int sexpm_adjoint(sexpm_plan_t* p, double tau, const sexpm_csr_view* W, int32_t ckpt_stride, sexpm_result_t** dH,
+                  sexpm_result_t** expm_out) {
+  SX_API_BEGIN
+  if (!p || !W || !dH) fail(SEXPM_EINVAL, "null argument");
+  *dH = nullptr;
+  if (expm_out) *expm_out = nullptr;
+  if (p->count > 0) fail(SEXPM_EINVAL, "the adjoint takes a plain (non-batched) plan");
+  if (W->n != p->H.n) fail(SEXPM_EINVAL, "W must have the dimension of H");
+  if (ckpt_stride < 0) fail(SEXPM_EINVAL, "ckpt_stride must be >= 0");
+  cudaStream_t s = p->s;
+  HostScalars& hs = p->hs;
+  const sexpm_options& o = p->opt;
+  Record rec;
+  rec.stride = ckpt_stride;
+  sexpm_result* fwd = new sexpm_result();
+  sexpm_result* res = new sexpm_result();
+  try {
+    // forward with every product formed (the reverse pass differentiates exactly this map)
+    compute_impl(p, tau, fwd, &rec, false);
+    Timer t_all(s);
+    CsrOwned Wd;
+    upload(*W, s, Wd, hs);
+    const CsrD Hp = p->H.view();
+    res->s = s;
+    std::memset(&res->st, 0, sizeof(res->st));
+    res->st = fwd->st;
+    res->steps = fwd->steps;
+    res->E.n = Hp.n;
+    res->E.nnz = Hp.nnz;
+    res->E.rp.reset(Hp.n + 1, s);
+    res->E.ci.reset(Hp.nnz, s);
+    res->E.v.reset(Hp.nnz, s);
+    SX_CUDA(cudaMemcpyAsync(res->E.rp.p, Hp.rp, (Hp.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    if (Hp.nnz) SX_CUDA(cudaMemcpyAsync(res->E.ci.p, Hp.ci, Hp.nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    CsrD none;
+    if (rec.M == 0) {
+      // ||tau H|| = 0: the method returns I; its first-order term is tau H, so dL/dH = tau W
+      sddmm(Hp, Wd.view(), none, 0.0, 1.0, false, res->E.v.p, s, hs);
+      scale_values(res->E.v.p, tau, Hp.nnz, res->E.v.p, s);
+    } else {
+      const int N = rec.N;
+      // dL/dT_N = W on the pattern of T^_N
+      CsrD TN = rec.T.at(N).view();
+      DevBuf<double> y(TN.nnz, s);
+      sddmm(TN, Wd.view(), none, 0.0, 1.0, false, y.p, s, hs);
+      CsrD Ypat = TN;                 // pattern of the current adjoint Y
+      CsrOwned Ykeep;                 // owns Y's pattern when it is not a checkpoint
+      std::map<int, CsrOwned> seg;    // replayed iterates of the current checkpoint segment
+      RowStats rs;
+      for (int k = N; k >= 1; --k) {
+        // T^_{k-1}: a checkpoint, or replayed from the checkpoint below it
+        const int km1 = k - 1;
+        if (!rec.T.count(km1) && !seg.count(km1)) {
+          seg.clear();
+          int c = km1;
+          while (!rec.T.count(c)) --c;
+          CsrD cur = rec.T.at(c).view();
+          for (int j = c + 1; j <= km1; ++j) {
+            square_step(o, cur, j, rec.a, rec.r0, false, s, hs, rs, seg[j], nullptr);
+            cur = seg[j].view();
+          }
+        }
+        const CsrD Tp = rec.T.count(km1) ? rec.T.at(km1).view() : seg.at(km1).view();
+        // dL/dT_{k-1} = mask_{k-1}(2 Y + Y T^T + T^T Y)
+        const CsrD Y = with_values(Ypat, y.p);
+        CsrOwned Tpt, Yt;
+        transpose(Tp, s, Tpt, hs);
+        transpose(Y, s, Yt, hs);
+        DevBuf<double> g(Tp.nnz, s);
+        sddmm(Tp, Y, Tp, 1.0, 2.0, false, g.p, s, hs);
+        sddmm(Tp, Tpt.view(), Yt.view(), 1.0, 0.0, true, g.p, s, hs);
+        y = std::move(g);
+        // the new Y lives on the pattern of T^_{k-1}; keep that pattern alive
+        if (rec.T.count(km1)) {
+          Ypat = rec.T.at(km1).view();
+          Ykeep = CsrOwned();
+        } else {
+          CsrOwned pat;
+          copy_csr(Tp, s, pat);
+          Ykeep = std::move(pat);
+          Ypat = Ykeep.view();
+        }
+        if (rec.T.count(k) && k != N) { /* checkpoints stay until the end */ }
+        seg.erase(k);
+      }
+      // Taylor phase: dL/dS_i = dL/dT_0 on the pattern of S_i, then i = M'..2
+      const int Mp = (int)rec.S.size();
+      std::vector<DevBuf<double>> gs(Mp);
+      const CsrD GT0 = with_values(Ypat, y.p);
+      for (int i = 0; i < Mp; ++i) {
+        gs[i].reset(rec.S[i].nnz, s);
+        sddmm(rec.S[i].view(), GT0, none, 0.0, 1.0, false, gs[i].p, s, hs);
+      }
+      DevBuf<double> gh(Hp.nnz, s);
+      SX_CUDA(cudaMemsetAsync(gh.p, 0, Hp.nnz * sizeof(double), s));
+      const CsrD H0 = rec.H0.view();
+      for (int i = Mp; i >= 2; --i) {
+        const CsrD Yi = with_values(rec.S[i - 1].view(), gs[i - 1].p);
+        const CsrD Sp = rec.S[i - 2].view();
+        sddmm(Sp, Yi, H0, 1.0 / i, 0.0, true, gs[i - 2].p, s, hs);          // += mask(Y H_0^T)/i
+        CsrOwned Spt, Yit;
+        transpose(Sp, s, Spt, hs);
+        transpose(Yi, s, Yit, hs);
+        sddmm(Hp, Spt.view(), Yit.view(), 1.0 / i, 0.0, true, gh.p, s, hs);  // += mask_H(S^T Y)/i
+      }
+      sddmm(Hp, with_values(rec.S[0].view(), gs[0].p), none, 0.0, 1.0, true, gh.p, s, hs);  // += dL/dS_1
+      scale_values(gh.p, tau * std::ldexp(1.0, -N), Hp.nnz, res->E.v.p, s);
+    }
+    SX_CUDA(cudaStreamSynchronize(s));
+    res->st.ms_total = fwd->st.ms_total + t_all.ms();
+    res->st.nnz_out = res->E.nnz;
+  } catch (...) {
+    delete fwd;
+    delete res;
+    throw;
+  }
+  *dH = res;
+  if (expm_out) *expm_out = fwd; else delete fwd;
   SX_API_END
 }
 

@@ -662,8 +662,8 @@ void transpose(const CsrD& A, cudaStream_t s, CsrOwned& T, HostScalars& hs) {
   SX_CUDA(cudaMemsetAsync(cnt.p, 0, cnt.count * sizeof(int32_t), s));
   if (n) {
     k_transpose_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, T.rp.p, cnt.p, T.ci.p, T.v.p);
-    k_sort_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, T.rp.p, T.ci.p, T.v.p);
-    count_launches(2);
+    count_launches(1);
+    sort_rows(n, T.rp.p, T.ci.p, T.v.p, s);
   }
   SX_CUDA(cudaGetLastError());
 }

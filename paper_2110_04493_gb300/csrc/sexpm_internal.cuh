@@ -180,4 +180,12 @@ void block_put(const CsrD& X, int64_t row0, int64_t nnz0, int64_t* rp, int32_t* 
 void block_get(const CsrD& E, int64_t row0, int64_t nb, int64_t nnz_b, CsrOwned& out, cudaStream_t s);
 void gather_row_ptr(const int64_t* rp, const int64_t* seg, int count, int64_t* out_host, cudaStream_t s);
 
+// ---------------------------------------------------------------- adjoint helpers
+// out[p] = (accumulate ? out[p] : 0) + alpha sum_l A_il B_jl + beta A_ij for every stored (i, j)
+// of P (out has P.nnz entries in P's order).
+void sddmm(const CsrD& P, const CsrD& A, const CsrD& B, double alpha, double beta, bool accumulate, double* out,
+           cudaStream_t s, HostScalars& hs);
+// Sorts the columns (with their values) of every row in place.
+void sort_rows(int64_t n, const int64_t* rp, int32_t* ci, double* v, cudaStream_t s);
+
 }  // namespace sexpm

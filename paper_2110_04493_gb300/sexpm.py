@@ -95,6 +95,7 @@ def load() -> ctypes.CDLL:
                                P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_double)]
     L.sexpm_plan_batched.argtypes = [P(CsrView), ctypes.c_int32, ctypes.c_double, P(Options), vp, P(vp)]
     L.sexpm_compute_batched.argtypes = [vp, P(ctypes.c_double), P(vp)]
+    L.sexpm_adjoint.argtypes = [vp, ctypes.c_double, P(CsrView), ctypes.c_int32, P(vp), P(vp)]
     L.sexpm_filter_noalloc.argtypes = [P(CsrView), ctypes.c_double, ctypes.c_double, ctypes.c_int32, vp, vp, vp, vp,
                                        ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_int32),
                                        P(ctypes.c_double)]
@@ -313,6 +314,34 @@ def expm_batched(Hs, taus, eps: float = 1e-12, device="cuda", **opts):
     return out
 
 
+def adjoint(H, tau: float, eps: float, W, ckpt_stride: int = 0, device="cuda", want_expm: bool = False, **opts):
+    """dL/dH on the pattern of H for dL/dE = W (E = e^{tau H}) through sexpm_adjoint.
+    Returns (row_ptr, col, val) of dH (and ((row_ptr, col, val), stats) of E if want_expm)."""
+    plan = H if isinstance(H, Plan) else Plan(H, eps, **opts)
+    keep: List[Any] = []
+    w = _make_view(W, keep)
+    r, e = ctypes.c_void_p(), ctypes.c_void_p()
+    try:
+        _check(load().sexpm_adjoint(plan._h, float(tau), ctypes.byref(w), int(ckpt_stride), ctypes.byref(r),
+                                    ctypes.byref(e) if want_expm else None))
+        res = Result(r.value)
+        try:
+            g = res.to_torch(device)
+            st = res.stats()
+        finally:
+            res.free()
+        if want_expm:
+            er = Result(e.value)
+            try:
+                return g, (er.to_torch(device), er.stats())
+            finally:
+                er.free()
+        return g
+    finally:
+        if plan is not H:
+            plan.close()
+
+
 def spgemm(A, B, D=None, div: float = 1.0, beta: float = 0.0, device="cuda"):
     """C = (A B)/div + beta D through sexpm_spgemm; returns ((row_ptr, col, val), products)."""
     keep: List[Any] = []
@@ -389,3 +418,42 @@ def choose_MN(norm_H: float, eps: float, n_extra: int = 50, max_M: int = 1000) -
     _check(load().sexpm_choose_MN(float(norm_H), float(eps), int(n_extra), int(max_M), ctypes.byref(M),
                                   ctypes.byref(N)))
     return M.value, N.value
+
+
+def _autograd_class():
+    import torch
+
+    class SexpmFn(torch.autograd.Function):
+        """e^{tau H} with a gradient: forward(h_val, row_ptr, col, n, tau, eps) returns the
+        values of E = e^{tau H} and its pattern (row_ptr, col, non-differentiable); backward
+        maps dL/d(E values) to dL/d(h_val) through sexpm_adjoint (masks frozen)."""
+
+        @staticmethod
+        def forward(ctx, h_val, row_ptr, col, n, tau, eps, ckpt_stride=0):
+            H = (row_ptr, col, h_val.detach(), int(n))
+            (erp, eci, ev), st = expm(H, tau, eps, device=h_val.device, symmetric=0)
+            ctx.save_for_backward(h_val.detach(), row_ptr, col, erp, eci)
+            ctx.n, ctx.tau, ctx.eps, ctx.stride = int(n), float(tau), float(eps), int(ckpt_stride)
+            ctx.mark_non_differentiable(erp, eci)
+            return ev, erp, eci
+
+        @staticmethod
+        def backward(ctx, g_ev, g_erp=None, g_eci=None):
+            h_val, row_ptr, col, erp, eci = ctx.saved_tensors
+            W = (erp, eci, g_ev.contiguous(), ctx.n)
+            _, _, g = adjoint((row_ptr, col, h_val, ctx.n), ctx.tau, ctx.eps, W, ckpt_stride=ctx.stride,
+                              device=h_val.device, symmetric=0)
+            return g, None, None, None, None, None, None
+
+    return SexpmFn
+
+
+_sexpm_fn = None
+
+
+def expm_autograd(h_val, row_ptr, col, n, tau, eps, ckpt_stride=0):
+    """Differentiable e^{tau H}: returns (E values, E row_ptr, E col); gradients flow to h_val."""
+    global _sexpm_fn
+    if _sexpm_fn is None:
+        _sexpm_fn = _autograd_class()
+    return _sexpm_fn.apply(h_val, row_ptr, col, n, tau, eps, ckpt_stride)
