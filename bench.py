@@ -198,6 +198,69 @@ def measure_batched(sexpm, torch, steps: int = 2):
             "launches_batched": int(l_batched), "launches_loop": int(l_loop), "steps": steps}
 
 
+def measure_adjoint(sexpm, torch, fd_edges: int = 0):
+    """Adjoint form on the random-geometric-graph workload: H = beta A (n = 1e5, mean degree 10,
+    weights U[0.5, 1.5], beta = 0.5, eps = 1e-12), L = sum_ij W_ij [e^H]_ij with 1e5 seeded
+    entries of W; dL/dA_e = beta (dL/dH_uv + dL/dH_vu) on every edge.  Times the plain forward
+    and the adjoint (its own forward plus the reverse pass) and, optionally, checks fd_edges
+    random edges against central differences of the GPU forward."""
+    import numpy as np
+    import scipy.sparse as sp
+    from workloads import rgg_adjacency, sparse_loss_weights
+    beta, eps, n = 0.5, 1e-12, 100_000
+    A = rgg_adjacency(n, seed=3)
+    W = sparse_loss_weights(n, 100_000, seed=3)
+    dev = lambda M, vals=None: (torch.from_numpy(M.row_ptr).cuda(), torch.from_numpy(M.col).cuda(),
+                                torch.from_numpy(M.val if vals is None else vals).cuda(), M.n)
+    Hv = beta * A.val
+    plan = sexpm.Plan(dev(A, Hv), eps)
+    plan.compute(1.0).free()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = plan.compute(1.0)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    st = res.stats()
+    res.free()
+    t0 = time.perf_counter()
+    rp, ci, g = sexpm.adjoint(plan, 1.0, eps, dev(W))
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    plan.close()
+    G = sp.csr_matrix((g.cpu().numpy(), A.col, A.row_ptr), shape=(n, n))
+    out = {"workload": "RGG n=1e5, mean degree 10, H = 0.5 A, eps 1e-12, W with 1e5 entries",
+           "M": st["M"], "N": st["N"], "nnz_expm": st["nnz_out"], "forward_ms": 1000.0 * t_fwd,
+           "adjoint_ms": 1000.0 * t_adj, "adjoint_over_forward": t_adj / t_fwd}
+    if fd_edges:
+        Ws = W.to_scipy()
+        Au = sp.triu(A.to_scipy(), 1).tocoo()
+        rng = np.random.default_rng(3)
+        pick = rng.choice(Au.nnz, size=fd_edges, replace=False)
+        Acsr = A.to_scipy()
+
+        def loss(vals):
+            (erp, eci, ev), _ = sexpm.expm(dev(A, beta * vals), 1.0, eps, symmetric=0)
+            E = sp.csr_matrix((ev.cpu().numpy(), eci.cpu().numpy(), erp.cpu().numpy()), shape=(n, n))
+            return float(E.multiply(Ws).sum())
+
+        worst = 0.0
+        gmax = float(np.abs(G).max()) if G.nnz else 0.0
+        for e in pick:
+            u, v = int(Au.row[e]), int(Au.col[e])
+            puv = A.row_ptr[u] + np.searchsorted(A.col[A.row_ptr[u]:A.row_ptr[u + 1]], v)
+            pvu = A.row_ptr[v] + np.searchsorted(A.col[A.row_ptr[v]:A.row_ptr[v + 1]], u)
+            d = 1e-4 * A.val[puv]
+            vp, vm = A.val.copy(), A.val.copy()
+            vp[[puv, pvu]] += d
+            vm[[puv, pvu]] -= d
+            fd = (loss(vp) - loss(vm)) / (2 * d)
+            ad = beta * (G[u, v] + G[v, u])
+            worst = max(worst, abs(ad - fd) / max(abs(fd), abs(ad), 1e-9 * beta * gmax, 1e-300))
+        out.update({"fd_edges": int(fd_edges), "fd_max_rel_err": worst,
+                    "fd_rel_err_floor": "max(|fd|, |adjoint|, 1e-9 max|dL/dA|)"})
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -307,7 +370,7 @@ def run_ours(args):
 
     forms = None
     if args.forms:
-        forms = {"batched": measure_batched(sexpm, torch)}
+        forms = {"adjoint": measure_adjoint(sexpm, torch, args.fd_edges), "batched": measure_batched(sexpm, torch)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -369,6 +432,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--per-step", action="store_true", help="add the per-step records to the JSON line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fd-edges", type=int, default=0,
+                    help="with --forms: check the adjoint on this many random edges by finite differences")
     ap.add_argument("--forms", action="store_true",
                     help="also time the batched form against the per-matrix loop (several minutes)")
     ap.add_argument("--sample-m", type=int, default=80,

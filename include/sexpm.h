@@ -73,6 +73,10 @@ typedef struct {
                                filter) and every squaring T~_i = 2T + T T, symmetric by
                                construction, forms only the entries at columns >= row and
                                mirrors the rest (halves the FP64 work); 0: form every entry */
+  int32_t row_order;        /* 1 (default): when H is a stencil on a grid numbered x + m y (+ m^2 z),
+                               the sparse products visit the rows in strips of 32 consecutive x for
+                               cache locality (the results do not depend on the order); 0: natural
+                               row order */
 } sexpm_options;
 
 typedef struct sexpm_plan sexpm_plan_t;

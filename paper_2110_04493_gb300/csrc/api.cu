@@ -206,6 +206,55 @@ void copy_csr(const CsrD& A, cudaStream_t s, CsrOwned& out) {
   }
 }
 
+// Row schedule for cache locality.  When H looks like a stencil on a grid numbered
+// x + m y (+ m^2 z) -- most rows store the offsets +-1 and +-m -- the products hand rows to
+// the thread blocks in strips of kStrip consecutive x: all y (and z) of one strip before the
+// next.  Rows processed together then read the B rows of a band about kStrip + (stencil
+// radius) wide instead of whole grid lines, which keeps the B operand resident in L2.
+// Returns the detected stride m (0 if none) and fills sched.
+constexpr int kStrip = 32;
+int64_t grid_schedule(const CsrOwned& H, cudaStream_t s, DevBuf<int32_t>& sched) {
+  const int64_t n = H.n;
+  if (n < 4 * kStrip * kStrip) return 0;
+  std::vector<int64_t> rp(n + 1);
+  std::vector<int32_t> ci(H.nnz);
+  SX_CUDA(cudaMemcpyAsync(rp.data(), H.rp.p, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  if (H.nnz) SX_CUDA(cudaMemcpyAsync(ci.data(), H.ci.p, H.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SX_CUDA(cudaStreamSynchronize(s));
+  // most frequent offset > 1 among the entries above the diagonal
+  std::map<int64_t, int64_t> freq;
+  const int64_t step = std::max<int64_t>(1, n / 20000);
+  int64_t sampled = 0;
+  for (int64_t i = 0; i < n; i += step, ++sampled)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const int64_t d = (int64_t)ci[p] - i;
+      if (d > 1) ++freq[d];
+    }
+  int64_t m = 0, best = 0;
+  for (const auto& kv : freq)
+    if (kv.second > best) { best = kv.second; m = kv.first; }
+  if (m < 2 * kStrip || best < sampled / 2) return 0;
+  // most sampled rows must also hold +1 (a grid line), else this is not a grid numbering
+  int64_t ones = 0;
+  for (int64_t i = 0; i < n; i += step)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+      if ((int64_t)ci[p] == i + 1) { ++ones; break; }
+  if (ones < sampled / 2) return 0;
+  std::vector<int32_t> order;
+  order.reserve(n);
+  const int64_t lines = (n + m - 1) / m;
+  for (int64_t x0 = 0; x0 < m; x0 += kStrip)
+    for (int64_t y = 0; y < lines; ++y)
+      for (int64_t x = x0; x < std::min<int64_t>(x0 + kStrip, m); ++x) {
+        const int64_t i = x + m * y;
+        if (i < n) order.push_back((int32_t)i);
+      }
+  sched.reset(n, s);
+  SX_CUDA(cudaMemcpyAsync(sched.p, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  SX_CUDA(cudaStreamSynchronize(s));
+  return m;
+}
+
 // Algorithm 4.2 step 2: exact symmetry, and normality (H = H^T or H = -H^T exactly, else
 // ||H H^T - H^T H||_F <= 64 u ||H||_F^2), unless overridden.
 void classify_matrix(const CsrOwned& H, int normal_override, cudaStream_t s, HostScalars& hs, bool& symmetric,
@@ -313,6 +362,9 @@ struct sexpm_plan {
   std::vector<char> symmetric_b;
   DevBuf<int64_t> seg;
   DevBuf<int32_t> inst;
+  // row schedule of the sparse products (empty: natural order)
+  DevBuf<int32_t> sched;
+  int64_t grid_stride = 0;
 };
 
 struct sexpm_result {
@@ -339,14 +391,14 @@ struct Record {
 // One filtered incremental squaring T^_k = filter(2 T^_{k-1} + T^_{k-1}^2) (Eq. 4.15 with the
 // threshold of reading 8); deterministic, so a replay reproduces the forward exactly.
 void square_step(const sexpm_options& o, const CsrD& T, int k, double a, double r0, bool sym, cudaStream_t s,
-                 HostScalars& hs, RowStats& rs, CsrOwned& Tn, sexpm_step_stats* rec) {
+                 HostScalars& hs, RowStats& rs, CsrOwned& Tn, sexpm_step_stats* rec, const int32_t* sched) {
   Timer ts(s);
   const int64_t n = T.n;
   const double ri = std::ldexp(r0, k);
   CsrOwned Tt;
   SpgemmTimes tm;
   int64_t done = 0;
-  const int64_t prod = spgemm(T, T, T, 1.0, 2.0, s, Tt, &rs, hs, &tm, sym, &done);
+  const int64_t prod = spgemm(T, T, T, 1.0, 2.0, s, Tt, &rs, hs, &tm, sym, &done, nullptr, sched);
   const double flops = 2.0 * (double)done + 2.0 * (double)T.nnz;
   double normF = 1.0;
   if (o.square_scale) {
@@ -463,7 +515,8 @@ void compute_impl(sexpm_plan_t* p, double tau, sexpm_result* res, Record* record
     CsrOwned St;
     SpgemmTimes tm;
     int64_t done = 0;
-    const int64_t prod = spgemm(Sv, H0, none, (double)i, 0.0, s, St, nullptr, hs, &tm, false, &done);
+    const int64_t prod = spgemm(Sv, H0, none, (double)i, 0.0, s, St, nullptr, hs, &tm, false, &done, nullptr,
+                                p->sched.p);
     CsrOwned Sn;
     FilterOut fo = filter_alg41(St.view(), eps_g0, o.e_r, o.max_filter_iters, s, Sn, hs);
     sexpm_step_stats rec;
@@ -518,7 +571,7 @@ void compute_impl(sexpm_plan_t* p, double tau, sexpm_result* res, Record* record
   for (int i = 1; i <= N; ++i) {
     CsrOwned Tn;
     sexpm_step_stats rec;
-    square_step(o, T.view(), i, a, r0, sym, s, hs, rs, Tn, &rec);
+    square_step(o, T.view(), i, a, r0, sym, s, hs, rs, Tn, &rec, p->sched.p);
     T = std::move(Tn);
     res->steps.push_back(rec);
     if (record && (i % record->stride == 0 || i == N)) copy_csr(T.view(), s, record->T[i]);
@@ -582,6 +635,7 @@ int sexpm_options_default(sexpm_options* opt) {
   opt->n_extra = 50;
   opt->max_taylor = 1000;
   opt->symmetric = 1;
+  opt->row_order = 1;
   return SEXPM_OK;
 }
 
@@ -591,6 +645,7 @@ static void check_options(const sexpm_options& o) {
   if (o.normal_override < -1 || o.normal_override > 1) fail(SEXPM_EINVAL, "normal_override must be -1, 0 or 1");
   if (o.max_filter_iters < 1 || o.n_extra < 0 || o.max_taylor < 1) fail(SEXPM_EINVAL, "bad iteration limits");
   if (o.symmetric != 0 && o.symmetric != 1) fail(SEXPM_EINVAL, "symmetric must be 0 or 1");
+  if (o.row_order != 0 && o.row_order != 1) fail(SEXPM_EINVAL, "row_order must be 0 or 1");
 }
 
 int sexpm_plan(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_options* opt, void* stream,
@@ -609,6 +664,7 @@ int sexpm_plan(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_optio
     p->eps = eps;
     upload(*H, p->s, p->H, p->hs);
     classify_matrix(p->H, p->opt.normal_override, p->s, p->hs, p->symmetric, p->normal);
+    if (p->opt.row_order) p->grid_stride = grid_schedule(p->H, p->s, p->sched);
     SX_CUDA(cudaStreamSynchronize(p->s));
   } catch (...) {
     delete p;
@@ -1088,7 +1144,7 @@ int sexpm_adjoint(sexpm_plan_t* p, double tau, const sexpm_csr_view* W, int32_t 
           while (!rec.T.count(c)) --c;
           CsrD cur = rec.T.at(c).view();
           for (int j = c + 1; j <= km1; ++j) {
-            square_step(o, cur, j, rec.a, rec.r0, false, s, hs, rs, seg[j], nullptr);
+            square_step(o, cur, j, rec.a, rec.r0, false, s, hs, rs, seg[j], nullptr, p->sched.p);
             cur = seg[j].view();
           }
         }

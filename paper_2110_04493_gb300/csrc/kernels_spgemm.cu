@@ -40,7 +40,7 @@ constexpr int kClasses = 6;
 // Shared-memory budget and block size of each row class; the last class uses global scratch.
 // With at most 64 registers per thread, 256-thread blocks of up to 56 KB run four per SM.
 constexpr int kClassBytes[kClasses] = {8 << 10, 24 << 10, 56 << 10, 112 << 10, 220 << 10, INT_MAX};
-constexpr int kClassThreads[kClasses] = {64, 128, 256, 256, 512, 512};
+constexpr int kClassThreads[kClasses] = {64, 128, 256, 256, 256, 512};
 
 __host__ __device__ constexpr int class_limit(int c) {
   return c == 0 ? (8 << 10) : c == 1 ? (24 << 10) : c == 2 ? (56 << 10) : c == 3 ? (112 << 10)
@@ -55,9 +55,11 @@ __host__ __device__ __forceinline__ long long acc_region(long long W, long long 
   return ((a > w ? a : w) + 15) & ~15ll;
 }
 // Position prefixes are stored as 16-bit counts when the row has fewer than 65536 entries.
+// cnt is the row's entry count, cacc the entries accumulated (the upper part in the
+// symmetric mode).
 __host__ __device__ __forceinline__ bool small_prefix(long long cnt) { return cnt < 65536; }
-__host__ __device__ __forceinline__ long long numeric_need(long long W, long long cnt) {
-  return acc_region(W, cnt) + 4 * W + (((small_prefix(cnt) ? 2 * W : 4 * W) + 15) & ~15ll);
+__host__ __device__ __forceinline__ long long numeric_need(long long W, long long cnt, long long cacc) {
+  return acc_region(W, cacc) + 4 * W + (((small_prefix(cnt) ? 2 * W : 4 * W) + 15) & ~15ll);
 }
 
 // Word pattern of a CSR matrix: row r touches words wi[rp[r] .. rp[r+1]) with masks wb[...].
@@ -239,23 +241,25 @@ __global__ void k_analysis(CsrD A, CsrD B, CsrD D, const uint8_t* frozen, int32_
 // Assign each row to a class by its shared-memory need (bytes); append row ids per class and
 // record the largest need of each class (maxneed[class]).
 // mode 0: symbolic need 4 W; mode 1: numeric need 12 W + 8 cnt.
-__global__ void k_classify(int64_t n, const int32_t* words, const int64_t* rp_out, int mode,
-                           int32_t* lists, int64_t list_stride, unsigned long long* counts,
-                           unsigned long long* maxneed) {
+__global__ void k_classify(int64_t n, const int32_t* sched, const int32_t* words, const int64_t* rp_out,
+                           const int32_t* cnt_up, int mode, int32_t* lists, int64_t list_stride,
+                           unsigned long long* counts, unsigned long long* maxneed) {
   __shared__ unsigned int cnt[kClasses];
   __shared__ unsigned long long off[kClasses];
   if (threadIdx.x < kClasses) cnt[threadIdx.x] = 0;
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = (t < n && sched) ? (int64_t)sched[t] : t;  // rows enter the lists in schedule order
   int cls = -1;
   unsigned int slot = 0;
   long long need = 0;
-  if (i < n) {
+  if (t < n) {
     const long long W = words[i];
     if (mode == 0) {
       need = 4 * W;
     } else {
-      need = numeric_need(W, rp_out[i + 1] - rp_out[i]);
+      const long long full = rp_out[i + 1] - rp_out[i];
+      need = numeric_need(W, full, cnt_up ? (long long)cnt_up[i] : full);
     }
     if (W > 0) {
       cls = 0;
@@ -345,8 +349,8 @@ __device__ unsigned block_exclusive_scan(unsigned* x, int W, unsigned* red) {
 // Symbolic pass: cnt[i] = number of distinct columns of row i of A B (+ pattern of D).
 template <bool GLOBAL>
 __global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const uint8_t* frozen, const int32_t* rows,
-                           int64_t nrows, const int32_t* base, const int32_t* words, int32_t* cnt, uint32_t* gscratch,
-                           int64_t gstride) {
+                           int64_t nrows, const int32_t* base, const int32_t* words, int32_t* cnt, int32_t* cnt_up,
+                           uint32_t* gscratch, int64_t gstride) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int red[32];
   uint32_t* bm = GLOBAL ? gscratch + (int64_t)blockIdx.x * gstride : reinterpret_cast<uint32_t*>(smem);
@@ -358,10 +362,23 @@ __global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const uint8_t* f
     __syncthreads();
     build_row_bitmap(A, WB, WD, hasD, i, wlo, bm, nullptr, false, frozen && frozen[i]);
     __syncthreads();
-    int c = 0;
-    for (int w = threadIdx.x; w < W; w += blockDim.x) c += __popc(bm[w]);
+    int c = 0, cu = 0;
+    const int iw = i >> 5;
+    const uint32_t imask = ~((1u << (i & 31)) - 1u);
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+      const uint32_t m = bm[w];
+      c += __popc(m);
+      if (cnt_up) {
+        const int wa = wlo + w;
+        cu += wa > iw ? __popc(m) : (wa == iw ? __popc(m & imask) : 0);
+      }
+    }
     c = block_sum(c, red);
     if (threadIdx.x == 0) cnt[i] = c;
+    if (cnt_up) {
+      cu = block_sum(cu, red);
+      if (threadIdx.x == 0) cnt_up[i] = cu;
+    }
     __syncthreads();
   }
 }
@@ -406,7 +423,8 @@ __device__ void block_popc_prefix(const uint32_t* bm, PreT* pre, int W, unsigned
 // and the ordered write.  acc/wk share the accumulator region; bm holds the row bitmap.
 template <typename PreT>
 __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, bool upper, bool fz,
-                            int i, int W, int b, int64_t o0, int cnt, double* acc, unsigned* wk, const uint32_t* bm,
+                            int i, int W, int b, int64_t o0, int cnt, int lo_pos, double* acc, unsigned* wk,
+                            const uint32_t* bm,
                             PreT* pre, int32_t* ci_out, double* v_out, double* row_sq, double* row_diag,
                             unsigned* ured, double* dred, unsigned long long* work_total) {
   const int nwarps = blockDim.x >> 5;
@@ -433,7 +451,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
       wb = (warp_id() == nwarps - 1) ? W : lo;
     }
     __syncthreads();  // every warp has read wk: the region now becomes the accumulator
-    for (int k = threadIdx.x; k < cnt; k += T) acc[k] = 0.0;
+    for (int k = lo_pos + threadIdx.x; k < cnt; k += T) acc[k] = 0.0;
     __syncthreads();
     if (wa < wb && !fz) {
       const int c_lo = upper ? max(b + 32 * wa, i) : b + 32 * wa;
@@ -456,58 +474,33 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
             }
           }
         }
-        const int nb = (int)(a1 - kb < 32 ? a1 - kb : 32);
-        // software pipeline: the first four chunks of the next segment are loaded while the
-        // current segment is accumulated.  All entries of one segment belong to one row B_k,
-        // so their columns (and positions) are distinct within a round.
-        int64_t sj = __shfl_sync(FULL, s, 0), ej = __shfl_sync(FULL, e, 0);
-        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-        {
-          const int64_t q = sj + lane;
-          if (q < ej) { c0 = __ldg(B.ci + q); v0 = __ldg(B.v + q); }
-          if (q + 32 < ej) { c1 = __ldg(B.ci + q + 32); v1 = __ldg(B.v + q + 32); }
-          if (q + 64 < ej) { c2 = __ldg(B.ci + q + 64); v2 = __ldg(B.v + q + 64); }
-          if (q + 96 < ej) { c3 = __ldg(B.ci + q + 96); v3 = __ldg(B.v + q + 96); }
-        }
-        for (int j = 0; j < nb; ++j) {
+        // only the non-empty segments of this batch of 32 k's are visited (ballot), each with
+        // 32-bit offsets and four independent chunks per round.  All entries of one segment
+        // belong to one row B_k, so their columns (and positions) are distinct within a round.
+        unsigned live = __ballot_sync(FULL, e > s);
+        while (live) {
+          const int j = __ffs(live) - 1;
+          live &= live - 1u;
           const double aj = __shfl_sync(FULL, a, j);
-          const int jn = j + 1 < nb ? j + 1 : j;
-          const int64_t sn = __shfl_sync(FULL, s, jn);
-          const int64_t en = j + 1 < nb ? __shfl_sync(FULL, e, jn) : sn;
-          int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-          double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
-          {
-            const int64_t q = sn + lane;
-            if (q < en) { n0 = __ldg(B.ci + q); u0 = __ldg(B.v + q); }
-            if (q + 32 < en) { n1 = __ldg(B.ci + q + 32); u1 = __ldg(B.v + q + 32); }
-            if (q + 64 < en) { n2 = __ldg(B.ci + q + 64); u2 = __ldg(B.v + q + 64); }
-            if (q + 96 < en) { n3 = __ldg(B.ci + q + 96); u3 = __ldg(B.v + q + 96); }
-          }
-          const int64_t q = sj + lane;
-          if (q < ej) { const int pp = (int)rank_of(bm, pre, c0 - b); acc[pp] = fma(aj, v0, acc[pp]); }
-          if (q + 32 < ej) { const int pp = (int)rank_of(bm, pre, c1 - b); acc[pp] = fma(aj, v1, acc[pp]); }
-          if (q + 64 < ej) { const int pp = (int)rank_of(bm, pre, c2 - b); acc[pp] = fma(aj, v2, acc[pp]); }
-          if (q + 96 < ej) { const int pp = (int)rank_of(bm, pre, c3 - b); acc[pp] = fma(aj, v3, acc[pp]); }
-          // rest of a long segment
-          for (int64_t qq = sj + 128 + lane; qq < ej; qq += 128) {
-            const bool m1 = qq + 32 < ej, m2 = qq + 64 < ej, m3 = qq + 96 < ej;
-            const int d0 = __ldg(B.ci + qq);
-            const double x0 = __ldg(B.v + qq);
+          const int64_t sj = __shfl_sync(FULL, s, j);
+          const int len = (int)(__shfl_sync(FULL, e, j) - sj);
+          const int32_t* __restrict__ cb = B.ci + sj;
+          const double* __restrict__ vb = B.v + sj;
+          for (int q = lane; q < len; q += 128) {
+            const bool m1 = q + 32 < len, m2 = q + 64 < len, m3 = q + 96 < len;
+            const int d0 = __ldg(cb + q);
+            const double x0 = __ldg(vb + q);
             int d1 = 0, d2 = 0, d3 = 0;
             double x1 = 0.0, x2 = 0.0, x3 = 0.0;
-            if (m1) { d1 = __ldg(B.ci + qq + 32); x1 = __ldg(B.v + qq + 32); }
-            if (m2) { d2 = __ldg(B.ci + qq + 64); x2 = __ldg(B.v + qq + 64); }
-            if (m3) { d3 = __ldg(B.ci + qq + 96); x3 = __ldg(B.v + qq + 96); }
+            if (m1) { d1 = __ldg(cb + q + 32); x1 = __ldg(vb + q + 32); }
+            if (m2) { d2 = __ldg(cb + q + 64); x2 = __ldg(vb + q + 64); }
+            if (m3) { d3 = __ldg(cb + q + 96); x3 = __ldg(vb + q + 96); }
             { const int pp = (int)rank_of(bm, pre, d0 - b); acc[pp] = fma(aj, x0, acc[pp]); }
             if (m1) { const int pp = (int)rank_of(bm, pre, d1 - b); acc[pp] = fma(aj, x1, acc[pp]); }
             if (m2) { const int pp = (int)rank_of(bm, pre, d2 - b); acc[pp] = fma(aj, x2, acc[pp]); }
             if (m3) { const int pp = (int)rank_of(bm, pre, d3 - b); acc[pp] = fma(aj, x3, acc[pp]); }
           }
           __syncwarp();
-          sj = sn; ej = en;
-          c0 = n0; c1 = n1; c2 = n2; c3 = n3;
-          v0 = u0; v1 = u1; v2 = u2; v3 = u3;
         }
       }
     }
@@ -516,7 +509,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
   // 4. scaling (Taylor /i) and the fused beta D term (squaring +2T), in that order;
   //    a frozen row is a plain copy of D
   if (div != 1.0)
-    for (int k = threadIdx.x; k < cnt; k += T) acc[k] = acc[k] / div;
+    for (int k = lo_pos + threadIdx.x; k < cnt; k += T) acc[k] = acc[k] / div;
   __syncthreads();
   if (hasD) {
     const double coef = fz ? 1.0 : beta;
@@ -536,7 +529,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
   for (int k = threadIdx.x; k < cnt; k += T) {
     const int col = b + column_at(bm, pre, W, k);
     ci_out[o0 + k] = col;
-    if (upper && col < i) continue;
+    if (k < lo_pos) continue;
     const double v = acc[k];
     v_out[o0 + k] = v;
     sq += (upper && col != i) ? 2.0 * v * v : v * v;
@@ -554,7 +547,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
 // prefixes (16- or 32-bit).
 template <bool GLOBAL>
 __global__ void k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, double beta, bool upper,
-                          const uint8_t* frozen, const int32_t* rows,
+                          const uint8_t* frozen, const int32_t* cnt_up, const int32_t* rows,
                           int64_t nrows, const int32_t* base, const int32_t* words, const int64_t* rp_out,
                           int32_t* ci_out, double* v_out, double* row_sq, double* row_diag, unsigned char* gscratch,
                           int64_t gstride, unsigned long long* work_total) {
@@ -570,9 +563,10 @@ __global__ void k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, 
     const int b = base[i];
     const int64_t o0 = rp_out[i];
     const int cnt = (int)(rp_out[i + 1] - o0);
-    double* acc = reinterpret_cast<double*>(mem);
+    const int cacc = upper ? cnt_up[i] : cnt;   // entries accumulated: positions cnt - cacc .. cnt
+    double* acc = reinterpret_cast<double*>(mem) - (cnt - cacc);  // indexed by full-row position
     unsigned* wk = reinterpret_cast<unsigned*>(mem);
-    uint32_t* bm = reinterpret_cast<uint32_t*>(mem + acc_region(W, cnt));
+    uint32_t* bm = reinterpret_cast<uint32_t*>(mem + acc_region(W, cacc));
     for (int w = threadIdx.x; w < W; w += T) {
       bm[w] = 0u;
       wk[w] = 0u;
@@ -584,10 +578,11 @@ __global__ void k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, 
     build_row_bitmap(A, WB, WD, hasD, i, b >> 5, bm, wk, upper, fz);
     __syncthreads();
     if (small_prefix(cnt))
-      numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, acc, wk, bm,
+      numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, cnt - cacc, acc, wk, bm,
                   reinterpret_cast<unsigned short*>(bm + W), ci_out, v_out, row_sq, row_diag, ured, dred, work_total);
     else
-      numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, acc, wk, bm, reinterpret_cast<unsigned*>(bm + W),
+      numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, cnt - cacc, acc, wk, bm,
+                  reinterpret_cast<unsigned*>(bm + W),
                   ci_out, v_out, row_sq, row_diag, ured, dred, work_total);
   }
 }
@@ -614,12 +609,14 @@ __global__ void k_mirror(int64_t n, const int64_t* rp, const int32_t* ci, double
   }
 }
 
-__global__ void k_zero_rows(const int32_t* words, int64_t n, double* row_sq, double* row_diag, int32_t* cnt) {
+__global__ void k_zero_rows(const int32_t* words, int64_t n, double* row_sq, double* row_diag, int32_t* cnt,
+                            int32_t* cnt_up) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n && words[i] == 0) {
     if (row_sq) row_sq[i] = 0.0;
     if (row_diag) row_diag[i] = 0.0;
     cnt[i] = 0;
+    if (cnt_up) cnt_up[i] = 0;
   }
 }
 
@@ -709,7 +706,7 @@ void word_pattern(const CsrD& X, cudaStream_t s, WPatOwned& out, HostScalars& hs
 
 int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, cudaStream_t s, CsrOwned& C,
                RowStats* stats, HostScalars& hs, SpgemmTimes* times, bool upper, int64_t* done,
-               const uint8_t* frozen) {
+               const uint8_t* frozen, const int32_t* sched) {
   const int64_t n = A.n;
   EventPair ev_sym(times != nullptr, s), ev_num(times != nullptr, s);
   set_smem_limits();
@@ -734,6 +731,7 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
   const WPat WB = wB.view();
   const WPat WD = hasD ? (same ? WB : wD.view()) : WPat();
   DevBuf<int32_t> base(n, s), words(n, s), cnt(n, s), lists((size_t)n * kClasses, s);
+  DevBuf<int32_t> cnt_up(upper ? n : 0, s);
   DevBuf<int64_t> flops(n, s);
   DevBuf<unsigned long long> ctr(2 * kClasses + 4, s);
   SX_CUDA(cudaMemsetAsync(ctr.p, 0, ctr.count * sizeof(unsigned long long), s));
@@ -743,9 +741,11 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
     k_analysis<<<(unsigned)blocks, threads, 0, s>>>(A, B, D, frozen, base.p, words.p, flops.p);
     SX_CUDA(cudaGetLastError());
     k_sum_i64<<<(unsigned)std::min<int64_t>((n + 255) / 256, sms * 8), 256, 0, s>>>(flops.p, n, ctr.p + 2 * kClasses + 2);
-    k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, words.p, nullptr, 0, lists.p, n, ctr.p, ctr.p + kClasses);
+    k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, sched, words.p, nullptr, nullptr, 0, lists.p, n, ctr.p,
+                                                         ctr.p + kClasses);
     k_zero_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(words.p, n, stats ? stats->sq.p : nullptr,
-                                                         stats ? stats->diag.p : nullptr, cnt.p);
+                                                         stats ? stats->diag.p : nullptr, cnt.p,
+                                                         upper ? cnt_up.p : nullptr);
     SX_CUDA(cudaGetLastError());
     count_launches(4);
   }
@@ -765,13 +765,14 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 32);
         const int bytes = (int)((need + 1023) & ~1023ll);
         k_symbolic<false><<<(unsigned)grid, threads, bytes, s>>>(A, WB, WD, hasD, frozen, lists.p + c * n, nr,
-                                                               base.p, words.p, cnt.p, nullptr, 0);
+                                                               base.p, words.p, cnt.p, upper ? cnt_up.p : nullptr,
+                                                               nullptr, 0);
       } else {
         const int64_t stride = (need / 4 + 63) & ~63ll;
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
         gs.reset((size_t)(stride * grid), s);
         k_symbolic<true><<<(unsigned)grid, threads, 0, s>>>(A, WB, WD, hasD, frozen, lists.p + c * n, nr, base.p,
-                                                          words.p, cnt.p, gs.p, stride);
+                                                          words.p, cnt.p, upper ? cnt_up.p : nullptr, gs.p, stride);
       }
       SX_CUDA(cudaGetLastError());
       count_launches(1);
@@ -783,7 +784,8 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
   C.nnz = total;
   C.ci.reset(total, s);
   C.v.reset(total, s);
-  k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, words.p, C.rp.p, 1, lists.p, n, ctr.p, ctr.p + kClasses);
+  k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, sched, words.p, C.rp.p, upper ? cnt_up.p : nullptr, 1,
+                                                       lists.p, n, ctr.p, ctr.p + kClasses);
   SX_CUDA(cudaGetLastError());
   count_launches(1);
   SX_CUDA(cudaMemcpyAsync(h, ctr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -801,13 +803,14 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 32);
         const int bytes = (int)((need + 1023) & ~1023ll);
         k_numeric<false><<<(unsigned)grid, threads, bytes, s>>>(
-            A, B, D, WB, WD, div, beta, upper, frozen, lists.p + c * n, nr, base.p, words.p, C.rp.p, C.ci.p, C.v.p,
+            A, B, D, WB, WD, div, beta, upper, frozen, upper ? cnt_up.p : nullptr, lists.p + c * n, nr, base.p, words.p, C.rp.p, C.ci.p, C.v.p,
             stats ? stats->sq.p : nullptr, stats ? stats->diag.p : nullptr, nullptr, 0, ctr.p + 2 * kClasses + 3);
       } else {
         const int64_t stride = (need + 255) & ~255ll;
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
         gs.reset((size_t)(stride * grid), s);
-        k_numeric<true><<<(unsigned)grid, threads, 0, s>>>(A, B, D, WB, WD, div, beta, upper, frozen, lists.p + c * n,
+        k_numeric<true><<<(unsigned)grid, threads, 0, s>>>(A, B, D, WB, WD, div, beta, upper, frozen,
+                                                         upper ? cnt_up.p : nullptr, lists.p + c * n,
                                                          nr, base.p,
                                                          words.p, C.rp.p, C.ci.p, C.v.p, stats ? stats->sq.p : nullptr,
                                                          stats ? stats->diag.p : nullptr, gs.p, stride,

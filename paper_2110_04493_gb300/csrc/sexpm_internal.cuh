@@ -123,9 +123,11 @@ struct SpgemmTimes {
 // done (optional) receives the number of products actually formed.
 // frozen (optional, one byte per row): rows with frozen[i] != 0 form no products and are a plain
 // copy of D_i (used by the batched method for instances that have finished their squarings).
+// sched (optional, n row ids): the order in which rows are handed to the thread blocks (a
+// permutation chosen for cache locality; results do not depend on it).
 int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, cudaStream_t s,
                CsrOwned& C, RowStats* stats, HostScalars& hs, SpgemmTimes* times = nullptr, bool upper = false,
-               int64_t* done = nullptr, const uint8_t* frozen = nullptr);
+               int64_t* done = nullptr, const uint8_t* frozen = nullptr, const int32_t* sched = nullptr);
 
 // sum_i x[i] over n doubles, deterministic order.  Synchronises and returns the sum.
 double reduce_sum(const double* x, int64_t n, cudaStream_t s, HostScalars& hs);

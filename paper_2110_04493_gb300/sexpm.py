@@ -37,7 +37,7 @@ class CsrView(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("e_r", ctypes.c_double), ("square_scale", ctypes.c_int32), ("normal_override", ctypes.c_int32),
                 ("max_filter_iters", ctypes.c_int32), ("n_extra", ctypes.c_int32), ("max_taylor", ctypes.c_int32),
-                ("symmetric", ctypes.c_int32)]
+                ("symmetric", ctypes.c_int32), ("row_order", ctypes.c_int32)]
 
 
 class StepStats(ctypes.Structure):

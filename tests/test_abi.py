@@ -44,8 +44,8 @@ def test_library_exports_every_declared_symbol(lib):
 def test_options_default(lib):
     from paper_2110_04493_gb300 import sexpm
     o = sexpm.options()
-    assert (o.e_r, o.square_scale, o.normal_override, o.max_filter_iters, o.n_extra, o.symmetric) == \
-        (0.1, 1, -1, 100, 50, 1)
+    assert (o.e_r, o.square_scale, o.normal_override, o.max_filter_iters, o.n_extra, o.symmetric, o.row_order) == \
+        (0.1, 1, -1, 100, 50, 1, 1)
 
 
 def _rho_closed(M, x):

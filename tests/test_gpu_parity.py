@@ -242,3 +242,14 @@ def test_expm_rejects_invalid_input(sx):
         sx.expm(torch_csr(nanm), 1.0, 1e-12)
     with pytest.raises(sx.SexpmError):
         sx.expm(torch_csr(CSR.from_dense([[1.0]])), 1.0, 0.0)
+
+
+def test_row_schedule_does_not_change_results(sx):
+    """The strip schedule of grid-numbered matrices only reorders work: results are identical."""
+    H = dirichlet_laplacian(80, 2)
+    tau = 2.253 / 81 ** 2
+    (a_rp, a_ci, a_v), st1 = sx.expm(torch_csr(H), tau, 1e-12, row_order=1)
+    (b_rp, b_ci, b_v), st0 = sx.expm(torch_csr(H), tau, 1e-12, row_order=0)
+    assert np.array_equal(a_rp.cpu().numpy(), b_rp.cpu().numpy())
+    assert np.array_equal(a_ci.cpu().numpy(), b_ci.cpu().numpy())
+    assert np.array_equal(a_v.cpu().numpy(), b_v.cpu().numpy())
