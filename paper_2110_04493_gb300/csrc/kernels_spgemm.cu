@@ -475,32 +475,72 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
           }
         }
         // only the non-empty segments of this batch of 32 k's are visited (ballot), each with
-        // 32-bit offsets and four independent chunks per round.  All entries of one segment
-        // belong to one row B_k, so their columns (and positions) are distinct within a round.
+        // 32-bit offsets and four independent chunks per round; the first round of the next
+        // non-empty segment is loaded while the current one is accumulated.  All entries of one
+        // segment belong to one row B_k, so their columns (and positions) are distinct.
         unsigned live = __ballot_sync(FULL, e > s);
-        while (live) {
-          const int j = __ffs(live) - 1;
-          live &= live - 1u;
+        int j = live ? __ffs(live) - 1 : -1;
+        live &= live - 1u;
+        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        int64_t sj = 0;
+        int len = 0;
+        if (j >= 0) {
+          sj = __shfl_sync(FULL, s, j);
+          len = (int)(__shfl_sync(FULL, e, j) - sj);
+          const int32_t* cb = B.ci + sj;
+          const double* vb = B.v + sj;
+          if (lane < len) { c0 = __ldg(cb + lane); v0 = __ldg(vb + lane); }
+          if (lane + 32 < len) { c1 = __ldg(cb + lane + 32); v1 = __ldg(vb + lane + 32); }
+          if (lane + 64 < len) { c2 = __ldg(cb + lane + 64); v2 = __ldg(vb + lane + 64); }
+          if (lane + 96 < len) { c3 = __ldg(cb + lane + 96); v3 = __ldg(vb + lane + 96); }
+        }
+        while (j >= 0) {
           const double aj = __shfl_sync(FULL, a, j);
-          const int64_t sj = __shfl_sync(FULL, s, j);
-          const int len = (int)(__shfl_sync(FULL, e, j) - sj);
-          const int32_t* __restrict__ cb = B.ci + sj;
-          const double* __restrict__ vb = B.v + sj;
-          for (int q = lane; q < len; q += 128) {
-            const bool m1 = q + 32 < len, m2 = q + 64 < len, m3 = q + 96 < len;
-            const int d0 = __ldg(cb + q);
-            const double x0 = __ldg(vb + q);
-            int d1 = 0, d2 = 0, d3 = 0;
-            double x1 = 0.0, x2 = 0.0, x3 = 0.0;
-            if (m1) { d1 = __ldg(cb + q + 32); x1 = __ldg(vb + q + 32); }
-            if (m2) { d2 = __ldg(cb + q + 64); x2 = __ldg(vb + q + 64); }
-            if (m3) { d3 = __ldg(cb + q + 96); x3 = __ldg(vb + q + 96); }
-            { const int pp = (int)rank_of(bm, pre, d0 - b); acc[pp] = fma(aj, x0, acc[pp]); }
-            if (m1) { const int pp = (int)rank_of(bm, pre, d1 - b); acc[pp] = fma(aj, x1, acc[pp]); }
-            if (m2) { const int pp = (int)rank_of(bm, pre, d2 - b); acc[pp] = fma(aj, x2, acc[pp]); }
-            if (m3) { const int pp = (int)rank_of(bm, pre, d3 - b); acc[pp] = fma(aj, x3, acc[pp]); }
+          const int jn = live ? __ffs(live) - 1 : -1;
+          live &= live - 1u;
+          int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+          double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+          int64_t sn = 0;
+          int ln = 0;
+          if (jn >= 0) {
+            sn = __shfl_sync(FULL, s, jn);
+            ln = (int)(__shfl_sync(FULL, e, jn) - sn);
+            const int32_t* cb = B.ci + sn;
+            const double* vb = B.v + sn;
+            if (lane < ln) { n0 = __ldg(cb + lane); u0 = __ldg(vb + lane); }
+            if (lane + 32 < ln) { n1 = __ldg(cb + lane + 32); u1 = __ldg(vb + lane + 32); }
+            if (lane + 64 < ln) { n2 = __ldg(cb + lane + 64); u2 = __ldg(vb + lane + 64); }
+            if (lane + 96 < ln) { n3 = __ldg(cb + lane + 96); u3 = __ldg(vb + lane + 96); }
+          }
+          if (lane < len) { const int pp = (int)rank_of(bm, pre, c0 - b); acc[pp] = fma(aj, v0, acc[pp]); }
+          if (lane + 32 < len) { const int pp = (int)rank_of(bm, pre, c1 - b); acc[pp] = fma(aj, v1, acc[pp]); }
+          if (lane + 64 < len) { const int pp = (int)rank_of(bm, pre, c2 - b); acc[pp] = fma(aj, v2, acc[pp]); }
+          if (lane + 96 < len) { const int pp = (int)rank_of(bm, pre, c3 - b); acc[pp] = fma(aj, v3, acc[pp]); }
+          if (len > 128) {
+            const int32_t* __restrict__ cb = B.ci + sj;
+            const double* __restrict__ vb = B.v + sj;
+            for (int q = 128 + lane; q < len; q += 128) {
+              const bool m1 = q + 32 < len, m2 = q + 64 < len, m3 = q + 96 < len;
+              const int d0 = __ldg(cb + q);
+              const double x0 = __ldg(vb + q);
+              int d1 = 0, d2 = 0, d3 = 0;
+              double x1 = 0.0, x2 = 0.0, x3 = 0.0;
+              if (m1) { d1 = __ldg(cb + q + 32); x1 = __ldg(vb + q + 32); }
+              if (m2) { d2 = __ldg(cb + q + 64); x2 = __ldg(vb + q + 64); }
+              if (m3) { d3 = __ldg(cb + q + 96); x3 = __ldg(vb + q + 96); }
+              { const int pp = (int)rank_of(bm, pre, d0 - b); acc[pp] = fma(aj, x0, acc[pp]); }
+              if (m1) { const int pp = (int)rank_of(bm, pre, d1 - b); acc[pp] = fma(aj, x1, acc[pp]); }
+              if (m2) { const int pp = (int)rank_of(bm, pre, d2 - b); acc[pp] = fma(aj, x2, acc[pp]); }
+              if (m3) { const int pp = (int)rank_of(bm, pre, d3 - b); acc[pp] = fma(aj, x3, acc[pp]); }
+            }
           }
           __syncwarp();
+          j = jn;
+          sj = sn;
+          len = ln;
+          c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+          v0 = u0; v1 = u1; v2 = u2; v3 = u3;
         }
       }
     }
