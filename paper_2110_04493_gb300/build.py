@@ -54,7 +54,10 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every CUDA/C++ source and link libsexpm.so; returns its path."""
+    """Compile every CUDA/C++ source and link libsexpm.so; returns its path.
+
+    SEXPM_NVCC_FLAGS (environment) adds nvcc flags, e.g. -D overrides of tuning constants."""
+    extra = tuple(extra) + tuple(os.environ.get("SEXPM_NVCC_FLAGS", "").split())
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)

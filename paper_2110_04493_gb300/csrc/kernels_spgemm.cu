@@ -38,9 +38,10 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kClasses = 6;
 // Shared-memory budget and block size of each row class; the last class uses global scratch.
-// With at most 64 registers per thread, 256-thread blocks of up to 56 KB run four per SM.
+// Blocks have at most 256 threads; the numeric kernel is compiled for SEXPM_NUMERIC_BLOCKS
+// resident 256-thread blocks per SM (its register budget).
 constexpr int kClassBytes[kClasses] = {8 << 10, 24 << 10, 56 << 10, 112 << 10, 220 << 10, INT_MAX};
-constexpr int kClassThreads[kClasses] = {64, 128, 256, 256, 256, 512};
+constexpr int kClassThreads[kClasses] = {64, 128, 256, 256, 256, 256};
 
 __host__ __device__ constexpr int class_limit(int c) {
   return c == 0 ? (8 << 10) : c == 1 ? (24 << 10) : c == 2 ? (56 << 10) : c == 3 ? (112 << 10)
@@ -585,8 +586,11 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
 // Numeric pass.  Layout per row: an accumulator region (acc[cnt] doubles; before the
 // accumulation it holds wk[W], the prefix product counts), bm[W] words, pre[W] position
 // prefixes (16- or 32-bit).
+#ifndef SEXPM_NUMERIC_BLOCKS
+#define SEXPM_NUMERIC_BLOCKS 4
+#endif
 template <bool GLOBAL>
-__global__ void k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, double beta, bool upper,
+__global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, double beta, bool upper,
                           const uint8_t* frozen, const int32_t* cnt_up, const int32_t* rows,
                           int64_t nrows, const int32_t* base, const int32_t* words, const int64_t* rp_out,
                           int32_t* ci_out, double* v_out, double* row_sq, double* row_diag, unsigned char* gscratch,
