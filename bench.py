@@ -255,9 +255,9 @@ def measure_adjoint(sexpm, torch, fd_edges: int = 0):
             vm[[puv, pvu]] -= d
             fd = (loss(vp) - loss(vm)) / (2 * d)
             ad = beta * (G[u, v] + G[v, u])
-            worst = max(worst, abs(ad - fd) / max(abs(fd), abs(ad), 1e-9 * beta * gmax, 1e-300))
+            worst = max(worst, abs(ad - fd) / max(abs(fd), abs(ad), 1e-3 * beta * gmax, 1e-300))
         out.update({"fd_edges": int(fd_edges), "fd_max_rel_err": worst,
-                    "fd_rel_err_floor": "max(|fd|, |adjoint|, 1e-9 max|dL/dA|)"})
+                    "fd_rel_err_floor": "max(|fd|, |adjoint|, 1e-3 max|dL/dA|)"})
     return out
 
 

@@ -1,0 +1,142 @@
+"""Checks at the full sizes of the benchmark workloads, where the CPU oracle cannot run:
+sampled outputs against closed forms, and e^H R against an independent time stepper."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from tests._compare import torch_csr
+from workloads import dirichlet_laplacian, get_config, rgg_adjacency, sparse_loss_weights
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sx():
+    from paper_2110_04493_gb300 import build as B
+    B.build()
+    from paper_2110_04493_gb300 import sexpm
+    sexpm.load()
+    return sexpm
+
+
+def _sine_basis_expm(m, tau):
+    h = 1.0 / (m + 1)
+    j = np.arange(1, m + 1)
+    lam = -(4.0 / h ** 2) * np.sin(j * np.pi * h / 2) ** 2
+    V = np.sqrt(2 * h) * np.sin(np.outer(j, j) * np.pi * h)
+    return (V * np.exp(tau * lam)) @ V.T
+
+
+def _rows(rp, ci, v, rows):
+    """Dense copies of the given rows of a device CSR (col, val) pairs."""
+    rph = rp.cpu().numpy()
+    out = []
+    for i in rows:
+        a, b = int(rph[i]), int(rph[i + 1])
+        out.append((ci[a:b].cpu().numpy(), v[a:b].cpu().numpy()))
+    return out
+
+
+def test_lap2d_m1500_rows_match_kronecker_closed_form(sx):
+    """The bench workload (n = 2.25M): 48 sampled full rows of e^{tau L} against
+    e^{tau L_1} (x) e^{tau L_1} (1-D sine eigenbasis), max-abs <= 1e-12 ||e^H||_1 (<= 1e-12)."""
+    c = get_config("lap2d_m1500")
+    H = c.build()
+    (rp, ci, v), st = sx.expm(torch_csr(H), c.tau, c.eps)
+    m = 1500
+    E1 = _sine_basis_expm(m, c.tau)
+    rng = np.random.default_rng(5)
+    rows = list(rng.integers(0, H.n, size=40)) + [0, m - 1, H.n - 1, H.n // 2, 37 * m + 3, 750 * m + 750, m * (m - 1), 1]
+    for i, (cols, vals) in zip(rows, _rows(rp, ci, v, rows)):
+        xi, yi = i % m, i // m
+        exact = np.outer(E1[yi], E1[xi]).ravel()
+        got = np.zeros(H.n)
+        got[cols] = vals
+        assert np.abs(got - exact).max() <= 1e-12, i
+    assert (st["M"], st["N"]) == (18, 14)
+
+
+def test_lap3d_rows_match_kronecker_closed_form(sx):
+    """The 3-D workload's tau/h^2 = 2.1125 and eps = 1e-12 on a 32^3 grid (the 64^3 grid's
+    unfiltered products exceed one GPU's memory in this build): sampled rows against
+    e^{tau L_1} (x) e^{tau L_1} (x) e^{tau L_1}."""
+    m = 32
+    tau = 2.1125 / (m + 1) ** 2
+    H = dirichlet_laplacian(m, 3)
+    (rp, ci, v), st = sx.expm(torch_csr(H), tau, 1e-12)
+    E1 = _sine_basis_expm(m, tau)
+    rng = np.random.default_rng(6)
+    rows = list(rng.integers(0, H.n, size=24)) + [0, H.n - 1, H.n // 2]
+    for i, (cols, vals) in zip(rows, _rows(rp, ci, v, rows)):
+        x, y, z = i % m, (i // m) % m, i // (m * m)
+        exact = np.einsum("a,b,c->abc", E1[z], E1[y], E1[x]).ravel()
+        got = np.zeros(H.n)
+        got[cols] = vals
+        assert np.abs(got - exact).max() <= 1e-12, i
+
+
+def test_rgg_1e5_expm_times_R_matches_time_stepper(sx):
+    """The differentiation workload's forward (RGG n = 1e5, H = 0.5 A, eps = 1e-12): e^H R for
+    four seeded vectors against a Taylor time stepper built on cuSPARSE SpMM (64 substeps,
+    terms until they fall below 1e-20 of the running sum)."""
+    import torch
+    A = rgg_adjacency(100_000, seed=3)
+    Hv = 0.5 * A.val
+    Hd = (torch.from_numpy(A.row_ptr).cuda(), torch.from_numpy(A.col).cuda(), torch.from_numpy(Hv).cuda(), A.n)
+    (rp, ci, v), st = sx.expm(Hd, 1.0, 1e-12)
+    E = torch.sparse_csr_tensor(rp, ci.to(torch.int64), v, size=(A.n, A.n))
+    Ht = torch.sparse_csr_tensor(Hd[0], Hd[1].to(torch.int64), Hd[2], size=(A.n, A.n))
+    R = torch.from_numpy(np.random.default_rng(7).uniform(-1, 1, (A.n, 4))).cuda()
+    Y = R.clone()
+    steps = 64
+    for _ in range(steps):
+        term, acc = Y.clone(), Y.clone()
+        for k in range(1, 60):
+            term = torch.sparse.mm(Ht, term) / (steps * k)
+            acc = acc + term
+            if term.abs().max() <= 1e-20 * acc.abs().max():
+                break
+        Y = acc
+    ER = torch.sparse.mm(E, R)
+    err = (ER - Y).abs().max().item() / Y.abs().max().item()
+    assert err <= 1e-11
+
+
+def test_rgg_1e5_adjoint_against_finite_differences(sx):
+    """dL/dA_e = 0.5 (dL/dH_uv + dL/dH_vu) on 8 random edges of the 1e5-node graph against
+    central differences of the GPU forward: relative error <= 1e-6, measured against
+    max(|fd|, 1e-3 max|dL/dH|) (below that the difference quotient's rounding noise,
+    ~1e-16 |L| / delta, dominates)."""
+    import torch
+    A = rgg_adjacency(100_000, seed=3)
+    W = sparse_loss_weights(A.n, 100_000, seed=3)
+    Ws = W.to_scipy()
+    dev = lambda vals: (torch.from_numpy(A.row_ptr).cuda(), torch.from_numpy(A.col).cuda(),
+                        torch.from_numpy(vals).cuda(), A.n)
+    rp, ci, g = sx.adjoint(dev(0.5 * A.val), 1.0, 1e-12, torch_csr(W))
+    G = sp.csr_matrix((g.cpu().numpy(), A.col, A.row_ptr), shape=(A.n, A.n))
+
+    def loss(vals):
+        (erp, eci, ev), _ = sx.expm(dev(0.5 * vals), 1.0, 1e-12, symmetric=0)
+        E = sp.csr_matrix((ev.cpu().numpy(), eci.cpu().numpy(), erp.cpu().numpy()), shape=(A.n, A.n))
+        return float(E.multiply(Ws).sum())
+
+    Au = sp.triu(A.to_scipy(), 1).tocoo()
+    rng = np.random.default_rng(3)
+    gmax = abs(G).max()
+    checked = 0
+    for e in rng.choice(Au.nnz, size=8, replace=False):
+        u, w = int(Au.row[e]), int(Au.col[e])
+        puw = A.row_ptr[u] + np.searchsorted(A.col[A.row_ptr[u]:A.row_ptr[u + 1]], w)
+        pwu = A.row_ptr[w] + np.searchsorted(A.col[A.row_ptr[w]:A.row_ptr[w + 1]], u)
+        d = 1e-4 * A.val[puw]
+        vp, vm = A.val.copy(), A.val.copy()
+        vp[[puw, pwu]] += d
+        vm[[puw, pwu]] -= d
+        fd = (loss(vp) - loss(vm)) / (2 * d)
+        ad = 0.5 * (G[u, w] + G[w, u])
+        assert abs(ad - fd) <= 1e-6 * max(abs(fd), abs(ad), 1e-3 * gmax), (u, w, ad, fd)
+        checked += 1
+    assert checked == 8
