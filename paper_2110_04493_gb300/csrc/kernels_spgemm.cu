@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <string>
 
 #include "sexpm_internal.cuh"
@@ -48,19 +49,34 @@ __host__ __device__ constexpr int class_limit(int c) {
        : c == 4 ? (220 << 10) : INT_MAX;
 }
 
+__host__ __device__ constexpr int class_warps(int c) { return (c == 0 ? 64 : c == 1 ? 128 : 256) / 32; }
+static_assert(class_warps(0) * 32 == kClassThreads[0] && class_warps(1) * 32 == kClassThreads[1] &&
+                  class_warps(2) * 32 == kClassThreads[2] && class_warps(5) * 32 == kClassThreads[5],
+              "class_warps must match kClassThreads");
+
+// Rows whose per-warp accumulators fit in ks_bytes bytes are accumulated with the k split
+// (each warp takes every nwarps-th k of A_i, whole rows B_k, into an accumulator of its own;
+// the accumulators are summed in warp order).  Short rows are latency-bound, and the k split
+// needs no per-k search and visits each B_k once.  ks_bytes = 0 disables it.
+constexpr int kKsplitBytesDefault = 16384;
+__host__ __device__ __forceinline__ bool ksplit_mode(long long cacc, int nwarps, int ks_bytes) {
+  return nwarps > 1 && 8 * cacc * nwarps <= ks_bytes;
+}
+
 // Shared bytes the numeric pass needs for a row with W bitmap words and cnt outputs: the
-// accumulator (8 cnt bytes, which first holds the per-word product counts, 4 W bytes),
-// the bitmap and the position prefix (4 W bytes each).
-__host__ __device__ __forceinline__ long long acc_region(long long W, long long cnt) {
-  const long long a = 8 * cnt, w = 4 * W;
+// accumulator (8 cnt bytes per accumulator, one or nwarps of them; the region first holds
+// the per-word product counts, 4 W bytes), the bitmap and the position prefix (4 W bytes each).
+__host__ __device__ __forceinline__ long long acc_region(long long W, long long cnt, int nwarps, int ks_bytes) {
+  const long long a = 8 * cnt * (ksplit_mode(cnt, nwarps, ks_bytes) ? nwarps : 1), w = 4 * W;
   return ((a > w ? a : w) + 15) & ~15ll;
 }
 // Position prefixes are stored as 16-bit counts when the row has fewer than 65536 entries.
 // cnt is the row's entry count, cacc the entries accumulated (the upper part in the
 // symmetric mode).
 __host__ __device__ __forceinline__ bool small_prefix(long long cnt) { return cnt < 65536; }
-__host__ __device__ __forceinline__ long long numeric_need(long long W, long long cnt, long long cacc) {
-  return acc_region(W, cacc) + 4 * W + (((small_prefix(cnt) ? 2 * W : 4 * W) + 15) & ~15ll);
+__host__ __device__ __forceinline__ long long numeric_need(long long W, long long cnt, long long cacc, int nwarps,
+                                                           int ks_bytes) {
+  return acc_region(W, cacc, nwarps, ks_bytes) + 4 * W + (((small_prefix(cnt) ? 2 * W : 4 * W) + 15) & ~15ll);
 }
 
 // Word pattern of a CSR matrix: row r touches words wi[rp[r] .. rp[r+1]) with masks wb[...].
@@ -243,7 +259,7 @@ __global__ void k_analysis(CsrD A, CsrD B, CsrD D, const uint8_t* frozen, int32_
 // record the largest need of each class (maxneed[class]).
 // mode 0: symbolic need 4 W; mode 1: numeric need 12 W + 8 cnt.
 __global__ void k_classify(int64_t n, const int32_t* sched, const int32_t* words, const int64_t* rp_out,
-                           const int32_t* cnt_up, int mode, int32_t* lists, int64_t list_stride,
+                           const int32_t* cnt_up, int mode, int ks_bytes, int32_t* lists, int64_t list_stride,
                            unsigned long long* counts, unsigned long long* maxneed) {
   __shared__ unsigned int cnt[kClasses];
   __shared__ unsigned long long off[kClasses];
@@ -256,15 +272,15 @@ __global__ void k_classify(int64_t n, const int32_t* sched, const int32_t* words
   long long need = 0;
   if (t < n) {
     const long long W = words[i];
-    if (mode == 0) {
-      need = 4 * W;
-    } else {
-      const long long full = rp_out[i + 1] - rp_out[i];
-      need = numeric_need(W, full, cnt_up ? (long long)cnt_up[i] : full);
-    }
+    const long long full = mode == 0 ? 0 : rp_out[i + 1] - rp_out[i];
+    const long long cacc = cnt_up ? (long long)cnt_up[i] : full;
     if (W > 0) {
       cls = 0;
-      while (cls < kClasses - 1 && need > class_limit(cls)) ++cls;
+      for (;;) {
+        need = mode == 0 ? 4 * W : numeric_need(W, full, cacc, class_warps(cls), ks_bytes);
+        if (cls == kClasses - 1 || need <= class_limit(cls)) break;
+        ++cls;
+      }
       slot = atomicAdd(&cnt[cls], 1u);
       atomicMax(&maxneed[cls], (unsigned long long)need);
     }
@@ -348,14 +364,27 @@ __device__ unsigned block_exclusive_scan(unsigned* x, int W, unsigned* red) {
 }
 
 // Symbolic pass: cnt[i] = number of distinct columns of row i of A B (+ pattern of D).
+// Dynamic row assignment for the persistent row kernels: block b first takes row b of its
+// list, then the rows gridDim.x, gridDim.x + 1, ... in the order blocks ask for them, so the
+// rows in flight stay a window of consecutive list entries (the list follows the row
+// schedule, which keeps the rows of B they read resident in L2).  Thread 0 asks at the start
+// of a row and publishes the answer after the row, so the atomic's latency is hidden; every
+// row body has a block barrier between the read of s_next and its next write.
+__device__ __forceinline__ long long next_row(unsigned long long* ctr) {
+  return (long long)gridDim.x + (long long)atomicAdd(ctr, 1ull);
+}
+
 template <bool GLOBAL>
 __global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const uint8_t* frozen, const int32_t* rows,
                            int64_t nrows, const int32_t* base, const int32_t* words, int32_t* cnt, int32_t* cnt_up,
-                           uint32_t* gscratch, int64_t gstride) {
+                           uint32_t* gscratch, int64_t gstride, unsigned long long* row_ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int red[32];
+  __shared__ long long s_next;
   uint32_t* bm = GLOBAL ? gscratch + (int64_t)blockIdx.x * gstride : reinterpret_cast<uint32_t*>(smem);
-  for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+  long long nxt = 0;
+  for (int64_t r = blockIdx.x; r < nrows;) {
+    if (threadIdx.x == 0) nxt = next_row(row_ctr);
     const int i = rows[r];
     const int W = words[i];
     const int wlo = base[i] >> 5;
@@ -380,7 +409,9 @@ __global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const uint8_t* f
       cu = block_sum(cu, red);
       if (threadIdx.x == 0) cnt_up[i] = cu;
     }
+    if (threadIdx.x == 0) s_next = nxt;
     __syncthreads();
+    r = s_next;
   }
 }
 
@@ -420,6 +451,36 @@ __device__ void block_popc_prefix(const uint32_t* bm, PreT* pre, int W, unsigned
   __syncthreads();
 }
 
+// acc[rank(c_t)] += aj * v_t for the NC chunks t = 0..NC-1 (lane + 32 t < rem, c_t >= c_lo).  The caller
+// guarantees that the active columns are distinct (they come from one row of B), so the
+// ranks are computed and the accumulators loaded for all chunks before any is stored, and
+// the chunks' DFMAs overlap.  rem is warp-uniform and every chunk has an active lane, so no
+// DFMA instruction is issued for a chunk without work.
+template <int NC, typename PreT>
+__device__ __forceinline__ void accumulate_chunks(double* acc, const uint32_t* bm, const PreT* pre, int b, double aj,
+                                                  int lane, int rem, int c_lo, const int* c, const double* v) {
+  int p[NC];
+  double x[NC];
+#pragma unroll
+  for (int t = 0; t < NC; ++t) p[t] = lane + 32 * t < rem && c[t] >= c_lo ? (int)rank_of(bm, pre, c[t] - b) : -1;
+#pragma unroll
+  for (int t = 0; t < NC; ++t) x[t] = p[t] >= 0 ? acc[p[t]] : 0.0;
+#pragma unroll
+  for (int t = 0; t < NC; ++t) x[t] = fma(aj, v[t], x[t]);
+#pragma unroll
+  for (int t = 0; t < NC; ++t)
+    if (p[t] >= 0) acc[p[t]] = x[t];
+}
+
+template <typename PreT>
+__device__ __forceinline__ void accumulate4(double* acc, const uint32_t* bm, const PreT* pre, int b, double aj,
+                                            int lane, int rem, int c_lo, const int* c, const double* v) {
+  if (rem > 96) accumulate_chunks<4>(acc, bm, pre, b, aj, lane, rem, c_lo, c, v);
+  else if (rem > 64) accumulate_chunks<3>(acc, bm, pre, b, aj, lane, rem, c_lo, c, v);
+  else if (rem > 32) accumulate_chunks<2>(acc, bm, pre, b, aj, lane, rem, c_lo, c, v);
+  else if (rem > 0) accumulate_chunks<1>(acc, bm, pre, b, aj, lane, rem, c_lo, c, v);
+}
+
 // Numeric pass, one row: prefixes, owner-computes accumulation, fused scaling and beta D,
 // and the ordered write.  acc/wk share the accumulator region; bm holds the row bitmap.
 template <typename PreT>
@@ -427,7 +488,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
                             int i, int W, int b, int64_t o0, int cnt, int lo_pos, double* acc, unsigned* wk,
                             const uint32_t* bm,
                             PreT* pre, int32_t* ci_out, double* v_out, double* row_sq, double* row_diag,
-                            unsigned* ured, double* dred, unsigned long long* work_total) {
+                            unsigned* ured, double* dred, unsigned long long* work_total, int ks_bytes) {
   const int nwarps = blockDim.x >> 5;
   const int T = blockDim.x;
   const int lane = lane_id();
@@ -436,14 +497,20 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
   block_popc_prefix(bm, pre, W, ured);
   const unsigned work = block_exclusive_scan(wk, W, ured);
   if (threadIdx.x == 0) atomicAdd(work_total, (unsigned long long)work);
-  // 3. owner-computes accumulation.  Warp w owns the words [wa, wb) that hold the w-th
-  //    equal share of the row's products, i.e. the columns [b + 32 wa, b + 32 wb).
+  // 3. accumulation, in one of two modes.
+  //    Column split: warp w owns the words [wa, wb) that hold the w-th equal share of the
+  //    row's products, i.e. the columns [b + 32 wa, b + 32 wb); it visits every k of A_i and
+  //    takes the part of B_k inside its columns (binary search).
+  //    k split (short rows): warp w takes the k's a0 + w, a0 + w + nwarps, ... and whole rows
+  //    B_k, into accumulator w (acc + w cacc); the accumulators are summed in warp order.
   {
-    const unsigned t0 = (unsigned)(((unsigned long long)warp_id() * work) / nwarps);
-    const unsigned t1 = (unsigned)(((unsigned long long)(warp_id() + 1) * work) / nwarps);
-    // first word whose prefix is >= target (words before it end before the target)
-    int wa = 0, wb = 0;
-    {
+    const bool ks = ksplit_mode(cnt - lo_pos, nwarps, ks_bytes);
+    const int cacc = cnt - lo_pos;
+    int wa = 0, wb = W;
+    if (!ks) {
+      const unsigned t0 = (unsigned)(((unsigned long long)warp_id() * work) / nwarps);
+      const unsigned t1 = (unsigned)(((unsigned long long)(warp_id() + 1) * work) / nwarps);
+      // first word whose prefix is >= target (words before it end before the target)
       int lo = 0, hi = W;
       while (lo < hi) { const int mid = (lo + hi) >> 1; if (wk[mid] < t0) lo = mid + 1; else hi = mid; }
       wa = lo;
@@ -451,27 +518,38 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
       while (lo < hi) { const int mid = (lo + hi) >> 1; if (wk[mid] < t1) lo = mid + 1; else hi = mid; }
       wb = (warp_id() == nwarps - 1) ? W : lo;
     }
-    __syncthreads();  // every warp has read wk: the region now becomes the accumulator
-    for (int k = lo_pos + threadIdx.x; k < cnt; k += T) acc[k] = 0.0;
+    __syncthreads();  // every warp has read wk: the region now becomes the accumulator(s)
+    const int zend = lo_pos + (ks ? nwarps : 1) * cacc;
+    for (int k = lo_pos + threadIdx.x; k < zend; k += T) acc[k] = 0.0;
     __syncthreads();
     if (wa < wb && !fz) {
       const int c_lo = upper ? max(b + 32 * wa, i) : b + 32 * wa;
       const int c_hi = b + 32 * wb - 1;
+      double* const accw = ks ? acc + warp_id() * cacc : acc;
       const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
-      for (int64_t kb = a0; kb < a1; kb += 32) {
-        const int64_t p = kb + lane;
+      const int64_t pstep = ks ? nwarps : 1;               // stride between this warp's k's
+      const int64_t pfirst = ks ? a0 + warp_id() : a0;
+      for (int64_t kb = pfirst; kb < a1; kb += 32 * pstep) {
+        const int64_t p = kb + lane * pstep;
         int64_t s = 0, e = 0;
         double a = 0.0;
         if (p < a1) {
           const int k = A.ci[p];
           a = A.v[p];
           const int64_t b0 = B.rp[k], b1 = B.rp[k + 1];
-          s = e = b0;
-          if (b1 > b0) {
+          s = b0;
+          e = b1;
+          if (ks) {
+            // whole row; in the upper mode long rows start at the first column >= c_lo,
+            // short ones are masked entry by entry
+            if (upper && b1 - b0 > 64 && B.ci[b0] < c_lo) s = lower_bound_col(B.ci, b0, b1, c_lo);
+          } else if (b1 > b0) {
             const int f = B.ci[b0], l = B.ci[b1 - 1];
             if (f <= c_hi && l >= c_lo) {
               s = f >= c_lo ? b0 : lower_bound_col(B.ci, b0, b1, c_lo);
               e = l <= c_hi ? b1 : lower_bound_col(B.ci, s, b1, c_hi + 1);
+            } else {
+              e = s;
             }
           }
         }
@@ -514,10 +592,11 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
             if (lane + 64 < ln) { n2 = __ldg(cb + lane + 64); u2 = __ldg(vb + lane + 64); }
             if (lane + 96 < ln) { n3 = __ldg(cb + lane + 96); u3 = __ldg(vb + lane + 96); }
           }
-          if (lane < len) { const int pp = (int)rank_of(bm, pre, c0 - b); acc[pp] = fma(aj, v0, acc[pp]); }
-          if (lane + 32 < len) { const int pp = (int)rank_of(bm, pre, c1 - b); acc[pp] = fma(aj, v1, acc[pp]); }
-          if (lane + 64 < len) { const int pp = (int)rank_of(bm, pre, c2 - b); acc[pp] = fma(aj, v2, acc[pp]); }
-          if (lane + 96 < len) { const int pp = (int)rank_of(bm, pre, c3 - b); acc[pp] = fma(aj, v3, acc[pp]); }
+          {
+            const int cc[4] = {c0, c1, c2, c3};
+            const double vv[4] = {v0, v1, v2, v3};
+            accumulate4(accw, bm, pre, b, aj, lane, len, c_lo, cc, vv);
+          }
           if (len > 128) {
             const int32_t* __restrict__ cb = B.ci + sj;
             const double* __restrict__ vb = B.v + sj;
@@ -530,10 +609,9 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
               if (m1) { d1 = __ldg(cb + q + 32); x1 = __ldg(vb + q + 32); }
               if (m2) { d2 = __ldg(cb + q + 64); x2 = __ldg(vb + q + 64); }
               if (m3) { d3 = __ldg(cb + q + 96); x3 = __ldg(vb + q + 96); }
-              { const int pp = (int)rank_of(bm, pre, d0 - b); acc[pp] = fma(aj, x0, acc[pp]); }
-              if (m1) { const int pp = (int)rank_of(bm, pre, d1 - b); acc[pp] = fma(aj, x1, acc[pp]); }
-              if (m2) { const int pp = (int)rank_of(bm, pre, d2 - b); acc[pp] = fma(aj, x2, acc[pp]); }
-              if (m3) { const int pp = (int)rank_of(bm, pre, d3 - b); acc[pp] = fma(aj, x3, acc[pp]); }
+              const int cc[4] = {d0, d1, d2, d3};
+              const double vv[4] = {x0, x1, x2, x3};
+              accumulate4(accw, bm, pre, b, aj, lane, len - (q - lane), c_lo, cc, vv);
             }
           }
           __syncwarp();
@@ -545,8 +623,16 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
         }
       }
     }
+    if (ks) {
+      __syncthreads();
+      for (int k = lo_pos + threadIdx.x; k < cnt; k += T) {
+        double v = acc[k];
+        for (int w = 1; w < nwarps; ++w) v += acc[k + w * cacc];
+        acc[k] = v;
+      }
+    }
   }
-  __syncthreads();
+  __syncthreads();  // every accumulation (and the k split's sum) is complete
   // 4. scaling (Taylor /i) and the fused beta D term (squaring +2T), in that order;
   //    a frozen row is a plain copy of D
   if (div != 1.0)
@@ -594,14 +680,18 @@ __global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, C
                           const uint8_t* frozen, const int32_t* cnt_up, const int32_t* rows,
                           int64_t nrows, const int32_t* base, const int32_t* words, const int64_t* rp_out,
                           int32_t* ci_out, double* v_out, double* row_sq, double* row_diag, unsigned char* gscratch,
-                          int64_t gstride, unsigned long long* work_total) {
+                          int64_t gstride, unsigned long long* work_total, unsigned long long* row_ctr,
+                          int ks_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned ured[32];
   __shared__ double dred[32];
+  __shared__ long long s_next;
   unsigned char* mem = GLOBAL ? gscratch + (int64_t)blockIdx.x * gstride : smem;
   const int T = blockDim.x;
   const bool hasD = D.n > 0;
-  for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+  long long nxt = 0;
+  for (int64_t r = blockIdx.x; r < nrows;) {
+    if (threadIdx.x == 0) nxt = next_row(row_ctr);
     const int i = rows[r];
     const int W = words[i];
     const int b = base[i];
@@ -610,7 +700,7 @@ __global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, C
     const int cacc = upper ? cnt_up[i] : cnt;   // entries accumulated: positions cnt - cacc .. cnt
     double* acc = reinterpret_cast<double*>(mem) - (cnt - cacc);  // indexed by full-row position
     unsigned* wk = reinterpret_cast<unsigned*>(mem);
-    uint32_t* bm = reinterpret_cast<uint32_t*>(mem + acc_region(W, cacc));
+    uint32_t* bm = reinterpret_cast<uint32_t*>(mem + acc_region(W, cacc, T >> 5, ks_bytes));
     for (int w = threadIdx.x; w < W; w += T) {
       bm[w] = 0u;
       wk[w] = 0u;
@@ -623,11 +713,15 @@ __global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, C
     __syncthreads();
     if (small_prefix(cnt))
       numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, cnt - cacc, acc, wk, bm,
-                  reinterpret_cast<unsigned short*>(bm + W), ci_out, v_out, row_sq, row_diag, ured, dred, work_total);
+                  reinterpret_cast<unsigned short*>(bm + W), ci_out, v_out, row_sq, row_diag, ured, dred, work_total,
+                  ks_bytes);
     else
       numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, cnt - cacc, acc, wk, bm,
                   reinterpret_cast<unsigned*>(bm + W),
-                  ci_out, v_out, row_sq, row_diag, ured, dred, work_total);
+                  ci_out, v_out, row_sq, row_diag, ured, dred, work_total, ks_bytes);
+    if (threadIdx.x == 0) s_next = nxt;
+    __syncthreads();
+    r = s_next;
   }
 }
 
@@ -680,6 +774,23 @@ int num_sms() {
     SX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
   return sms;
+}
+
+// Byte limit of the k split's accumulators: SEXPM_KSPLIT_BYTES from the environment (read on
+// every product, so a process can compare the two accumulation modes), else the default.
+int ksplit_bytes() {
+  const char* e = std::getenv("SEXPM_KSPLIT_BYTES");
+  if (!e || !*e) return kKsplitBytesDefault;
+  const long v = std::strtol(e, nullptr, 10);
+  return v < 0 ? 0 : (int)std::min<long>(v, 1l << 20);
+}
+
+// Blocks of `kernel` that are resident at once on the whole GPU (at least one per SM).
+template <typename K>
+int64_t resident_blocks(K kernel, int threads, int bytes) {
+  int per_sm = 0;
+  SX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, (size_t)bytes));
+  return (int64_t)std::max(per_sm, 1) * num_sms();
 }
 
 void set_smem_limits() {
@@ -767,6 +878,7 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
   }
   const bool hasD = D.n > 0;
   const int sms = num_sms();
+  const int ks_bytes = ksplit_bytes();
   ev_sym.start();
   WPatOwned wB, wD;
   word_pattern(B, s, wB, hs);
@@ -785,14 +897,17 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
     k_analysis<<<(unsigned)blocks, threads, 0, s>>>(A, B, D, frozen, base.p, words.p, flops.p);
     SX_CUDA(cudaGetLastError());
     k_sum_i64<<<(unsigned)std::min<int64_t>((n + 255) / 256, sms * 8), 256, 0, s>>>(flops.p, n, ctr.p + 2 * kClasses + 2);
-    k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, sched, words.p, nullptr, nullptr, 0, lists.p, n, ctr.p,
-                                                         ctr.p + kClasses);
+    k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, sched, words.p, nullptr, nullptr, 0, ks_bytes, lists.p,
+                                                         n, ctr.p, ctr.p + kClasses);
     k_zero_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(words.p, n, stats ? stats->sq.p : nullptr,
                                                          stats ? stats->diag.p : nullptr, cnt.p,
                                                          upper ? cnt_up.p : nullptr);
     SX_CUDA(cudaGetLastError());
     count_launches(4);
   }
+  // row counters of the dynamically scheduled symbolic and numeric launches, one per class each
+  DevBuf<unsigned long long> row_ctr(2 * kClasses, s);
+  SX_CUDA(cudaMemsetAsync(row_ctr.p, 0, row_ctr.count * sizeof(unsigned long long), s));
   unsigned long long h[2 * kClasses + 4];
   SX_CUDA(cudaMemcpyAsync(h, ctr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
   SX_CUDA(cudaStreamSynchronize(s));
@@ -806,17 +921,18 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
       const int threads = kClassThreads[c];
       const int64_t need = (int64_t)h[kClasses + c];
       if (c < kClasses - 1) {
-        const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 32);
         const int bytes = (int)((need + 1023) & ~1023ll);
+        const int64_t grid = std::min<int64_t>(nr, resident_blocks(k_symbolic<false>, threads, bytes));
         k_symbolic<false><<<(unsigned)grid, threads, bytes, s>>>(A, WB, WD, hasD, frozen, lists.p + c * n, nr,
                                                                base.p, words.p, cnt.p, upper ? cnt_up.p : nullptr,
-                                                               nullptr, 0);
+                                                               nullptr, 0, row_ctr.p + c);
       } else {
         const int64_t stride = (need / 4 + 63) & ~63ll;
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
         gs.reset((size_t)(stride * grid), s);
         k_symbolic<true><<<(unsigned)grid, threads, 0, s>>>(A, WB, WD, hasD, frozen, lists.p + c * n, nr, base.p,
-                                                          words.p, cnt.p, upper ? cnt_up.p : nullptr, gs.p, stride);
+                                                          words.p, cnt.p, upper ? cnt_up.p : nullptr, gs.p, stride,
+                                                          row_ctr.p + c);
       }
       SX_CUDA(cudaGetLastError());
       count_launches(1);
@@ -829,7 +945,7 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
   C.ci.reset(total, s);
   C.v.reset(total, s);
   k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, sched, words.p, C.rp.p, upper ? cnt_up.p : nullptr, 1,
-                                                       lists.p, n, ctr.p, ctr.p + kClasses);
+                                                       ks_bytes, lists.p, n, ctr.p, ctr.p + kClasses);
   SX_CUDA(cudaGetLastError());
   count_launches(1);
   SX_CUDA(cudaMemcpyAsync(h, ctr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -844,11 +960,12 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
       const int threads = kClassThreads[c];
       const int64_t need = (int64_t)h[kClasses + c];
       if (c < kClasses - 1) {
-        const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 32);
         const int bytes = (int)((need + 1023) & ~1023ll);
+        const int64_t grid = std::min<int64_t>(nr, resident_blocks(k_numeric<false>, threads, bytes));
         k_numeric<false><<<(unsigned)grid, threads, bytes, s>>>(
             A, B, D, WB, WD, div, beta, upper, frozen, upper ? cnt_up.p : nullptr, lists.p + c * n, nr, base.p, words.p, C.rp.p, C.ci.p, C.v.p,
-            stats ? stats->sq.p : nullptr, stats ? stats->diag.p : nullptr, nullptr, 0, ctr.p + 2 * kClasses + 3);
+            stats ? stats->sq.p : nullptr, stats ? stats->diag.p : nullptr, nullptr, 0, ctr.p + 2 * kClasses + 3,
+            row_ctr.p + kClasses + c, ks_bytes);
       } else {
         const int64_t stride = (need + 255) & ~255ll;
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
@@ -858,7 +975,7 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
                                                          nr, base.p,
                                                          words.p, C.rp.p, C.ci.p, C.v.p, stats ? stats->sq.p : nullptr,
                                                          stats ? stats->diag.p : nullptr, gs.p, stride,
-                                                         ctr.p + 2 * kClasses + 3);
+                                                         ctr.p + 2 * kClasses + 3, row_ctr.p + kClasses + c, ks_bytes);
       }
       SX_CUDA(cudaGetLastError());
       count_launches(1);

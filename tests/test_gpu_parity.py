@@ -253,3 +253,18 @@ def test_row_schedule_does_not_change_results(sx):
     assert np.array_equal(a_rp.cpu().numpy(), b_rp.cpu().numpy())
     assert np.array_equal(a_ci.cpu().numpy(), b_ci.cpu().numpy())
     assert np.array_equal(a_v.cpu().numpy(), b_v.cpu().numpy())
+
+
+@pytest.mark.parametrize("ks_bytes", ["0", "1048576"])
+def test_accumulation_modes_match_oracle(sx, monkeypatch, ks_bytes):
+    """Both accumulation modes of the numeric pass (column split: SEXPM_KSPLIT_BYTES=0; k split
+    wherever the per-warp accumulators fit: a large limit) against the oracle, on products with
+    long rows (the k split's upper-mode search) and on the symmetric method."""
+    monkeypatch.setenv("SEXPM_KSPLIT_BYTES", ks_bytes)
+    T = _ragged(2000, 21, dense_rows=(5, 1999), empty_rows=[2])
+    tt = torch_csr(_csr(T))
+    (rp, ci, v), _ = sx.spgemm(tt, tt, tt, div=1.0, beta=2.0)
+    _assert_product_parity(to_scipy(rp, ci, v, 2000), O.square_raw(T))
+    H = dirichlet_laplacian(40, 2)
+    _check_method(sx, H, 2.253 / 41 ** 2, 1e-12, symmetric=1)
+    _check_method(sx, H, 2.253 / 41 ** 2, 1e-12, symmetric=0)
