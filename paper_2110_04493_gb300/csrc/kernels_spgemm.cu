@@ -54,29 +54,46 @@ static_assert(class_warps(0) * 32 == kClassThreads[0] && class_warps(1) * 32 == 
                   class_warps(2) * 32 == kClassThreads[2] && class_warps(5) * 32 == kClassThreads[5],
               "class_warps must match kClassThreads");
 
-// Rows whose per-warp accumulators fit in ks_bytes bytes are accumulated with the k split
-// (each warp takes every nwarps-th k of A_i, whole rows B_k, into an accumulator of its own;
-// the accumulators are summed in warp order).  Short rows are latency-bound, and the k split
-// needs no per-k search and visits each B_k once.  ks_bytes = 0 disables it.
-constexpr int kKsplitBytesDefault = 16384;
-__host__ __device__ __forceinline__ bool ksplit_mode(long long cacc, int nwarps, int ks_bytes) {
-  return nwarps > 1 && 8 * cacc * nwarps <= ks_bytes;
-}
+// Position prefixes are stored as 16-bit counts when the row has fewer than 65536 entries.
+__host__ __device__ __forceinline__ bool small_prefix(long long cnt) { return cnt < 65536; }
 
-// Shared bytes the numeric pass needs for a row with W bitmap words and cnt outputs: the
-// accumulator (8 cnt bytes per accumulator, one or nwarps of them; the region first holds
-// the per-word product counts, 4 W bytes), the bitmap and the position prefix (4 W bytes each).
-__host__ __device__ __forceinline__ long long acc_region(long long W, long long cnt, int nwarps, int ks_bytes) {
-  const long long a = 8 * cnt * (ksplit_mode(cnt, nwarps, ks_bytes) ? nwarps : 1), w = 4 * W;
+// Shared bytes of the numeric pass for a row with W bitmap words, cnt outputs of which cacc
+// are accumulated (the upper part in the symmetric mode), and q accumulators: the
+// accumulators (8 cacc bytes each; the region first holds the per-word product counts,
+// 4 W bytes), the bitmap (4 W bytes) and the position prefix (2 or 4 W bytes).
+__host__ __device__ __forceinline__ long long acc_bytes(long long W, long long cacc, int q) {
+  const long long a = 8 * cacc * q, w = 4 * W;
   return ((a > w ? a : w) + 15) & ~15ll;
 }
-// Position prefixes are stored as 16-bit counts when the row has fewer than 65536 entries.
-// cnt is the row's entry count, cacc the entries accumulated (the upper part in the
-// symmetric mode).
-__host__ __device__ __forceinline__ bool small_prefix(long long cnt) { return cnt < 65536; }
+__host__ __device__ __forceinline__ long long need_bytes(long long W, long long cnt, long long cacc, int q) {
+  return acc_bytes(W, cacc, q) + 4 * W + (((small_prefix(cnt) ? 2 * W : 4 * W) + 15) & ~15ll);
+}
+
+// Accumulation layout of a row: the block's warps form groups of `members` warps.  The
+// groups split the row's columns (equal shares of its products); the members of a group
+// split the k's of A_i (member q takes every members-th k) and accumulate into accumulator q
+// of their own; the members' accumulators are summed in member order.  members = 1 is a pure
+// column split (every warp searches each B_k for its columns); members = nwarps is a pure
+// k split (whole rows B_k, no search).  More members means fewer, longer segments and fewer
+// searches, at 8 bytes per accumulated entry and member.  The numeric kernel holds 32 warps
+// per SM (its register budget), so a block of nwarps warps may use nwarps/32 of the SM's
+// shared memory without lowering that occupancy: members is the largest power of two whose
+// row fits in that share of sm_bytes (sm_bytes = 0: column split).
+constexpr int kKsplitBytesDefault = 220 << 10;
+__host__ __device__ __forceinline__ int ks_members(long long W, long long cnt, long long cacc, int nwarps,
+                                                   int sm_bytes) {
+  const long long budget = (long long)sm_bytes * nwarps / 32;
+  int q = nwarps;
+  while (q > 1 && need_bytes(W, cnt, cacc, q) > budget) q >>= 1;
+  return q;
+}
+__host__ __device__ __forceinline__ long long acc_region(long long W, long long cnt, long long cacc, int nwarps,
+                                                         int sm_bytes) {
+  return acc_bytes(W, cacc, ks_members(W, cnt, cacc, nwarps, sm_bytes));
+}
 __host__ __device__ __forceinline__ long long numeric_need(long long W, long long cnt, long long cacc, int nwarps,
-                                                           int ks_bytes) {
-  return acc_region(W, cacc, nwarps, ks_bytes) + 4 * W + (((small_prefix(cnt) ? 2 * W : 4 * W) + 15) & ~15ll);
+                                                           int sm_bytes) {
+  return need_bytes(W, cnt, cacc, ks_members(W, cnt, cacc, nwarps, sm_bytes));
 }
 
 // Word pattern of a CSR matrix: row r touches words wi[rp[r] .. rp[r+1]) with masks wb[...].
@@ -497,40 +514,39 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
   block_popc_prefix(bm, pre, W, ured);
   const unsigned work = block_exclusive_scan(wk, W, ured);
   if (threadIdx.x == 0) atomicAdd(work_total, (unsigned long long)work);
-  // 3. accumulation, in one of two modes.
-  //    Column split: warp w owns the words [wa, wb) that hold the w-th equal share of the
-  //    row's products, i.e. the columns [b + 32 wa, b + 32 wb); it visits every k of A_i and
-  //    takes the part of B_k inside its columns (binary search).
-  //    k split (short rows): warp w takes the k's a0 + w, a0 + w + nwarps, ... and whole rows
-  //    B_k, into accumulator w (acc + w cacc); the accumulators are summed in warp order.
+  // 3. accumulation.  Warp w is member q = w % members of group g = w / members; group g owns
+  //    the words [wa, wb) that hold the g-th equal share of the row's products, i.e. the
+  //    columns [b + 32 wa, b + 32 wb); member q visits the k's a0 + q, a0 + q + members, ...,
+  //    takes the part of B_k inside the group's columns (the whole row when there is one
+  //    group) and accumulates it into accumulator q (acc + q cacc).
   {
-    const bool ks = ksplit_mode(cnt - lo_pos, nwarps, ks_bytes);
     const int cacc = cnt - lo_pos;
+    const int members = ks_members(W, cnt, cacc, nwarps, ks_bytes);
+    const int groups = nwarps / members;
+    const int g = warp_id() / members, q = warp_id() % members;
     int wa = 0, wb = W;
-    if (!ks) {
-      const unsigned t0 = (unsigned)(((unsigned long long)warp_id() * work) / nwarps);
-      const unsigned t1 = (unsigned)(((unsigned long long)(warp_id() + 1) * work) / nwarps);
+    if (groups > 1) {
+      const unsigned t0 = (unsigned)(((unsigned long long)g * work) / groups);
+      const unsigned t1 = (unsigned)(((unsigned long long)(g + 1) * work) / groups);
       // first word whose prefix is >= target (words before it end before the target)
       int lo = 0, hi = W;
       while (lo < hi) { const int mid = (lo + hi) >> 1; if (wk[mid] < t0) lo = mid + 1; else hi = mid; }
       wa = lo;
       lo = wa; hi = W;
       while (lo < hi) { const int mid = (lo + hi) >> 1; if (wk[mid] < t1) lo = mid + 1; else hi = mid; }
-      wb = (warp_id() == nwarps - 1) ? W : lo;
+      wb = (g == groups - 1) ? W : lo;
     }
-    __syncthreads();  // every warp has read wk: the region now becomes the accumulator(s)
-    const int zend = lo_pos + (ks ? nwarps : 1) * cacc;
+    __syncthreads();  // every warp has read wk: the region now becomes the accumulators
+    const int zend = lo_pos + members * cacc;
     for (int k = lo_pos + threadIdx.x; k < zend; k += T) acc[k] = 0.0;
     __syncthreads();
     if (wa < wb && !fz) {
       const int c_lo = upper ? max(b + 32 * wa, i) : b + 32 * wa;
       const int c_hi = b + 32 * wb - 1;
-      double* const accw = ks ? acc + warp_id() * cacc : acc;
+      double* const accw = acc + q * cacc;
       const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
-      const int64_t pstep = ks ? nwarps : 1;               // stride between this warp's k's
-      const int64_t pfirst = ks ? a0 + warp_id() : a0;
-      for (int64_t kb = pfirst; kb < a1; kb += 32 * pstep) {
-        const int64_t p = kb + lane * pstep;
+      for (int64_t kb = a0 + q; kb < a1; kb += 32 * members) {
+        const int64_t p = kb + lane * members;
         int64_t s = 0, e = 0;
         double a = 0.0;
         if (p < a1) {
@@ -539,7 +555,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
           const int64_t b0 = B.rp[k], b1 = B.rp[k + 1];
           s = b0;
           e = b1;
-          if (ks) {
+          if (groups == 1) {
             // whole row; in the upper mode long rows start at the first column >= c_lo,
             // short ones are masked entry by entry
             if (upper && b1 - b0 > 64 && B.ci[b0] < c_lo) s = lower_bound_col(B.ci, b0, b1, c_lo);
@@ -623,11 +639,11 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
         }
       }
     }
-    if (ks) {
+    if (members > 1) {
       __syncthreads();
       for (int k = lo_pos + threadIdx.x; k < cnt; k += T) {
         double v = acc[k];
-        for (int w = 1; w < nwarps; ++w) v += acc[k + w * cacc];
+        for (int w = 1; w < members; ++w) v += acc[k + w * cacc];
         acc[k] = v;
       }
     }
@@ -700,7 +716,7 @@ __global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, C
     const int cacc = upper ? cnt_up[i] : cnt;   // entries accumulated: positions cnt - cacc .. cnt
     double* acc = reinterpret_cast<double*>(mem) - (cnt - cacc);  // indexed by full-row position
     unsigned* wk = reinterpret_cast<unsigned*>(mem);
-    uint32_t* bm = reinterpret_cast<uint32_t*>(mem + acc_region(W, cacc, T >> 5, ks_bytes));
+    uint32_t* bm = reinterpret_cast<uint32_t*>(mem + acc_region(W, cnt, cacc, T >> 5, ks_bytes));
     for (int w = threadIdx.x; w < W; w += T) {
       bm[w] = 0u;
       wk[w] = 0u;

@@ -255,11 +255,12 @@ def test_row_schedule_does_not_change_results(sx):
     assert np.array_equal(a_v.cpu().numpy(), b_v.cpu().numpy())
 
 
-@pytest.mark.parametrize("ks_bytes", ["0", "1048576"])
+@pytest.mark.parametrize("ks_bytes", ["0", "32768", "1048576"])
 def test_accumulation_modes_match_oracle(sx, monkeypatch, ks_bytes):
-    """Both accumulation modes of the numeric pass (column split: SEXPM_KSPLIT_BYTES=0; k split
-    wherever the per-warp accumulators fit: a large limit) against the oracle, on products with
-    long rows (the k split's upper-mode search) and on the symmetric method."""
+    """The accumulation layouts of the numeric pass against the oracle: pure column split
+    (SEXPM_KSPLIT_BYTES=0), groups of 1, 2, 4 or 8 k-splitting members chosen row by row (a
+    32 KB per-SM budget), and the pure k split wherever it fits (a 1 MB budget); on products
+    with long rows (the k split's upper-mode search) and on the method, symmetric and not."""
     monkeypatch.setenv("SEXPM_KSPLIT_BYTES", ks_bytes)
     T = _ragged(2000, 21, dense_rows=(5, 1999), empty_rows=[2])
     tt = torch_csr(_csr(T))
