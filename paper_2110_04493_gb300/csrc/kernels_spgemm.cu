@@ -54,19 +54,16 @@ static_assert(class_warps(0) * 32 == kClassThreads[0] && class_warps(1) * 32 == 
                   class_warps(2) * 32 == kClassThreads[2] && class_warps(5) * 32 == kClassThreads[5],
               "class_warps must match kClassThreads");
 
-// Position prefixes are stored as 16-bit counts when the row has fewer than 65536 entries.
-__host__ __device__ __forceinline__ bool small_prefix(long long cnt) { return cnt < 65536; }
-
 // Shared bytes of the numeric pass for a row with W bitmap words, cnt outputs of which cacc
 // are accumulated (the upper part in the symmetric mode), and q accumulators: the
 // accumulators (8 cacc bytes each; the region first holds the per-word product counts,
-// 4 W bytes), the bitmap (4 W bytes) and the position prefix (2 or 4 W bytes).
+// 4 W bytes) and the bitmap words with their position prefixes (8 W bytes).
 __host__ __device__ __forceinline__ long long acc_bytes(long long W, long long cacc, int q) {
   const long long a = 8 * cacc * q, w = 4 * W;
   return ((a > w ? a : w) + 15) & ~15ll;
 }
 __host__ __device__ __forceinline__ long long need_bytes(long long W, long long cnt, long long cacc, int q) {
-  return acc_bytes(W, cacc, q) + 4 * W + (((small_prefix(cnt) ? 2 * W : 4 * W) + 15) & ~15ll);
+  return acc_bytes(W, cacc, q) + 8 * W;
 }
 
 // Accumulation layout of a row: the block's warps form groups of `members` warps.  The
@@ -141,22 +138,25 @@ __device__ __forceinline__ int select_bit(uint32_t m, int r) {
   return pos;
 }
 
+// Row bitmap with position prefixes: word w of the row is bp[w] = {mask, prefix}, the mask of
+// the row's columns b + 32 w .. b + 32 w + 31 and the number of the row's columns before it.
 // Column (relative to the row base) of output position k: the largest word w with
-// pre[w] <= k, then the (k - pre[w])-th set bit of that word.
-template <typename PreT>
-__device__ __forceinline__ int column_at(const uint32_t* bm, const PreT* pre, int W, int k) {
+// prefix <= k, then the (k - prefix)-th set bit of that word.
+__device__ __forceinline__ int column_at(const uint2* bp, int W, int k) {
   int lo = 0, hi = W - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if ((int)pre[mid] <= k) lo = mid; else hi = mid - 1;
+    if ((int)bp[mid].y <= k) lo = mid; else hi = mid - 1;
   }
-  return lo * 32 + select_bit(bm[lo], k - (int)pre[lo]);
+  const uint2 e = bp[lo];
+  return lo * 32 + select_bit(e.x, k - (int)e.y);
 }
 
-template <typename PreT>
-__device__ __forceinline__ unsigned rank_of(const uint32_t* bm, const PreT* pre, int c) {
-  const int w = c >> 5;
-  return pre[w] + __popc(bm[w] & ((1u << (c & 31)) - 1u));
+// Output position of column c (relative to the row base): the prefix of its word plus the
+// set bits below it ((mask << (31 - r)) << 1 keeps bits 0 .. r-1 of the mask, r = c mod 32).
+__device__ __forceinline__ unsigned rank_of(const uint2* bp, int c) {
+  const uint2 e = bp[c >> 5];
+  return e.y + __popc((e.x << (~c & 31)) << 1);
 }
 
 __device__ __forceinline__ int64_t lower_bound_col(const int32_t* ci, int64_t lo, int64_t hi, int c) {
@@ -310,10 +310,11 @@ __global__ void k_classify(int64_t n, const int32_t* sched, const int32_t* words
 }
 
 // OR the word patterns of the rows B_k (k in A_i) and of D_i into the row bitmap bm
-// (word wlo of the row is bm[0]).  When work != nullptr, work[w] also receives the number of
+// (word wlo of the row is bm[0]; word w at bm[w * STRIDE]).  When work != nullptr, work[w] also receives the number of
 // scalar products that land in word w (the popcount of every B_k mask ORed into it).
 // Block-wide; the caller synchronises afterwards.
 // With upper set, only products at columns >= i are counted as work.
+template <int STRIDE>
 __device__ __forceinline__ void build_row_bitmap(const CsrD& A, const WPat& WB, const WPat& WD, bool hasD, int64_t i,
                                                  int wlo, uint32_t* bm, unsigned* work, bool upper, bool fz) {
   const int nwarps = blockDim.x >> 5;
@@ -327,7 +328,7 @@ __device__ __forceinline__ void build_row_bitmap(const CsrD& A, const WPat& WB, 
       const int wa = WB.wi[e];
       const int w = wa - wlo;
       const uint32_t bits = WB.wb[e];
-      atomicOr(&bm[w], bits);
+      atomicOr(&bm[w * STRIDE], bits);
       if (work) {
         const uint32_t wbits = !upper || wa > iw ? bits : (wa == iw ? (bits & imask) : 0u);
         if (wbits) atomicAdd(&work[w], (unsigned)__popc(wbits));
@@ -336,7 +337,7 @@ __device__ __forceinline__ void build_row_bitmap(const CsrD& A, const WPat& WB, 
   }
   if (hasD) {
     const int64_t e1 = WD.rp[i + 1];
-    for (int64_t e = WD.rp[i] + threadIdx.x; e < e1; e += blockDim.x) atomicOr(&bm[WD.wi[e] - wlo], WD.wb[e]);
+    for (int64_t e = WD.rp[i] + threadIdx.x; e < e1; e += blockDim.x) atomicOr(&bm[(WD.wi[e] - wlo) * STRIDE], WD.wb[e]);
   }
 }
 
@@ -407,7 +408,7 @@ __global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const uint8_t* f
     const int wlo = base[i] >> 5;
     for (int w = threadIdx.x; w < W; w += blockDim.x) bm[w] = 0u;
     __syncthreads();
-    build_row_bitmap(A, WB, WD, hasD, i, wlo, bm, nullptr, false, frozen && frozen[i]);
+    build_row_bitmap<1>(A, WB, WD, hasD, i, wlo, bm, nullptr, false, frozen && frozen[i]);
     __syncthreads();
     int c = 0, cu = 0;
     const int iw = i >> 5;
@@ -432,14 +433,13 @@ __global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const uint8_t* f
   }
 }
 
-// Exclusive prefix of popc(bm[w]) into pre[0..W) (type PreT) by the whole block.
-template <typename PreT>
-__device__ void block_popc_prefix(const uint32_t* bm, PreT* pre, int W, unsigned* red) {
+// Exclusive prefix of the popcounts of the masks bp[0..W).x into bp[0..W).y, by the whole block.
+__device__ void block_popc_prefix(uint2* bp, int W, unsigned* red) {
   const int T = blockDim.x, nwarps = T >> 5, lane = lane_id();
   const int ch = (W + T - 1) / T;
   const int w0 = min(W, (int)threadIdx.x * ch), w1 = min(W, w0 + ch);
   unsigned s = 0;
-  for (int w = w0; w < w1; ++w) s += __popc(bm[w]);
+  for (int w = w0; w < w1; ++w) s += __popc(bp[w].x);
   unsigned incl = s;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -462,63 +462,122 @@ __device__ void block_popc_prefix(const uint32_t* bm, PreT* pre, int W, unsigned
   __syncthreads();
   unsigned run = red[warp_id()] + incl - s;
   for (int w = w0; w < w1; ++w) {
-    pre[w] = (PreT)run;
-    run += __popc(bm[w]);
+    bp[w].y = run;
+    run += __popc(bp[w].x);
   }
   __syncthreads();
 }
 
-// acc[rank(c_t)] += aj * v_t for the NC chunks t = 0..NC-1 (lane + 32 t < rem, c_t >= c_lo).  The caller
-// guarantees that the active columns are distinct (they come from one row of B), so the
-// ranks are computed and the accumulators loaded for all chunks before any is stored, and
-// the chunks' DFMAs overlap.  rem is warp-uniform and every chunk has an active lane, so no
-// DFMA instruction is issued for a chunk without work.
-template <int NC, typename PreT>
-__device__ __forceinline__ void accumulate_chunks(double* acc, const uint32_t* bm, const PreT* pre, int b, double aj,
-                                                  int lane, int rem, int c_lo, const int* c, const double* v) {
-  int p[NC];
+// One quad of a segment: up to 128 consecutive entries of one row B_k, entry 32 t + lane of
+// the quad in chunk t of this lane.  s is the quad's first entry, len the entries left in the
+// segment from s, a the factor A_ik.
+struct Quad {
+  int64_t s;
+  int len;
+  double a;
+  int c[4];
+  double v[4];
+};
+
+// Loads the quad's four chunks.  Lanes past the segment's end read its last entry instead,
+// so every load is in bounds and none is conditional; such a lane repeats the last entry's
+// update (the same value, from the same accumulator load), which is harmless.
+__device__ __forceinline__ void load_quad(const CsrD& B, int lane, Quad& q) {
+  const int32_t* cb = B.ci + q.s;
+  const double* vb = B.v + q.s;
+  const int last = q.len - 1;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int e = min(lane + 32 * t, last);
+    q.c[t] = __ldg(cb + e);
+    q.v[t] = __ldg(vb + e);
+  }
+}
+
+// acc[rank(c_t)] += a v_t for the NC chunks of quad q; an entry with a column below c_lo (the
+// upper mode's entries below the diagonal) is sent to the warp's sink slot instead.  The
+// columns of a quad are distinct (one row of B; repeated last entries aside), so every rank
+// and accumulator load is issued before the first store and the chunks' DFMAs overlap.  The
+// code is branch-free; every chunk has a lane inside the segment, so no DFMA is issued for a
+// chunk without work.
+template <int NC>
+__device__ __forceinline__ void accumulate_chunks(double* acc, double* sink, const uint2* bp, int b, int c_lo,
+                                                  const Quad& q) {
+  double* ad[NC];
   double x[NC];
 #pragma unroll
-  for (int t = 0; t < NC; ++t) p[t] = lane + 32 * t < rem && c[t] >= c_lo ? (int)rank_of(bm, pre, c[t] - b) : -1;
+  for (int t = 0; t < NC; ++t) {
+    const int c = q.c[t];
+    double* const at = acc + rank_of(bp, c - b);
+    ad[t] = c >= c_lo ? at : sink;
+  }
 #pragma unroll
-  for (int t = 0; t < NC; ++t) x[t] = p[t] >= 0 ? acc[p[t]] : 0.0;
+  for (int t = 0; t < NC; ++t) x[t] = *ad[t];
 #pragma unroll
-  for (int t = 0; t < NC; ++t) x[t] = fma(aj, v[t], x[t]);
+  for (int t = 0; t < NC; ++t) x[t] = fma(q.a, q.v[t], x[t]);
 #pragma unroll
-  for (int t = 0; t < NC; ++t)
-    if (p[t] >= 0) acc[p[t]] = x[t];
+  for (int t = 0; t < NC; ++t) *ad[t] = x[t];
 }
 
-template <typename PreT>
-__device__ __forceinline__ void accumulate4(double* acc, const uint32_t* bm, const PreT* pre, int b, double aj,
-                                            int lane, int rem, int c_lo, const int* c, const double* v) {
-  if (rem > 96) accumulate_chunks<4>(acc, bm, pre, b, aj, lane, rem, c_lo, c, v);
-  else if (rem > 64) accumulate_chunks<3>(acc, bm, pre, b, aj, lane, rem, c_lo, c, v);
-  else if (rem > 32) accumulate_chunks<2>(acc, bm, pre, b, aj, lane, rem, c_lo, c, v);
-  else if (rem > 0) accumulate_chunks<1>(acc, bm, pre, b, aj, lane, rem, c_lo, c, v);
+__device__ __forceinline__ void accumulate_quad(double* acc, double* sink, const uint2* bp, int b, int c_lo,
+                                                const Quad& q) {
+  if (q.len > 96) accumulate_chunks<4>(acc, sink, bp, b, c_lo, q);
+  else if (q.len > 64) accumulate_chunks<3>(acc, sink, bp, b, c_lo, q);
+  else if (q.len > 32) accumulate_chunks<2>(acc, sink, bp, b, c_lo, q);
+  else accumulate_chunks<1>(acc, sink, bp, b, c_lo, q);
 }
 
-// Numeric pass, one row: prefixes, owner-computes accumulation, fused scaling and beta D,
-// and the ordered write.  acc/wk share the accumulator region; bm holds the row bitmap.
-template <typename PreT>
+// One stage of the accumulation pipeline: fix the quad after `cur` (the next 128 entries of
+// its segment, else the first quad of the next non-empty segment of the batch, from the
+// lanes' s, len, a and the mask `live` of segments not yet started), start its loads, then
+// accumulate `cur`.  Returns false when `cur` was the batch's last quad.  Between two
+// segments the warp synchronises: rows B_k and B_k' may share columns.
+__device__ __forceinline__ bool pipe_stage(const CsrD& B, double* acc, double* sink, const uint2* bp, int b,
+                                           int lane, int c_lo, int64_t s, int len, double a, unsigned& live,
+                                           const Quad& cur, Quad& nxt) {
+  bool more = true, fresh = false;
+  if (cur.len > 128) {
+    nxt.s = cur.s + 128;
+    nxt.len = cur.len - 128;
+    nxt.a = cur.a;
+  } else if (live) {
+    const int j = __ffs(live) - 1;
+    live &= live - 1u;
+    nxt.s = __shfl_sync(FULL, s, j);
+    nxt.len = __shfl_sync(FULL, len, j);
+    nxt.a = __shfl_sync(FULL, a, j);
+    fresh = true;
+  } else {
+    more = false;
+  }
+  if (more) load_quad(B, lane, nxt);
+  accumulate_quad(acc, sink, bp, b, c_lo, cur);
+  if (fresh) __syncwarp();
+  return more;
+}
+
+// Numeric pass, one row: prefixes, accumulation, fused scaling and beta D, and the ordered
+// write.  The accumulator region first holds wk (products per word); bp holds the row's
+// bitmap words with their position prefixes.
 __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, bool upper, bool fz,
                             int i, int W, int b, int64_t o0, int cnt, int lo_pos, double* acc, unsigned* wk,
-                            const uint32_t* bm,
-                            PreT* pre, int32_t* ci_out, double* v_out, double* row_sq, double* row_diag,
-                            unsigned* ured, double* dred, unsigned long long* work_total, int ks_bytes) {
+                            uint2* bp, double* sink, int32_t* ci_out, double* v_out, double* row_sq,
+                            double* row_diag, unsigned* ured, double* dred, unsigned long long* work_total,
+                            int ks_bytes) {
   const int nwarps = blockDim.x >> 5;
   const int T = blockDim.x;
   const int lane = lane_id();
   const bool hasD = D.n > 0;
-  // 2. exclusive prefixes: output positions (pre) and products (wk) per word
-  block_popc_prefix(bm, pre, W, ured);
+  // 2. exclusive prefixes: output positions (bp[].y) and products (wk) per word
+  block_popc_prefix(bp, W, ured);
   const unsigned work = block_exclusive_scan(wk, W, ured);
   if (threadIdx.x == 0) atomicAdd(work_total, (unsigned long long)work);
   // 3. accumulation.  Warp w is member q = w % members of group g = w / members; group g owns
   //    the words [wa, wb) that hold the g-th equal share of the row's products, i.e. the
   //    columns [b + 32 wa, b + 32 wb); member q visits the k's a0 + q, a0 + q + members, ...,
   //    takes the part of B_k inside the group's columns (the whole row when there is one
-  //    group) and accumulates it into accumulator q (acc + q cacc).
+  //    group) and accumulates it into accumulator q (acc + q cacc), one quad of 128 entries
+  //    at a time, loading the next quad while the current one is accumulated.
   {
     const int cacc = cnt - lo_pos;
     const int members = ks_members(W, cnt, cacc, nwarps, ks_bytes);
@@ -547,14 +606,15 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
       const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
       for (int64_t kb = a0 + q; kb < a1; kb += 32 * members) {
         const int64_t p = kb + lane * members;
-        int64_t s = 0, e = 0;
+        int64_t s = 0;
+        int len = 0;
         double a = 0.0;
         if (p < a1) {
           const int k = A.ci[p];
           a = A.v[p];
           const int64_t b0 = B.rp[k], b1 = B.rp[k + 1];
+          int64_t e = b1;
           s = b0;
-          e = b1;
           if (groups == 1) {
             // whole row; in the upper mode long rows start at the first column >= c_lo,
             // short ones are masked entry by entry
@@ -568,75 +628,24 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
               e = s;
             }
           }
+          len = (int)(e - s);
         }
-        // only the non-empty segments of this batch of 32 k's are visited (ballot), each with
-        // 32-bit offsets and four independent chunks per round; the first round of the next
-        // non-empty segment is loaded while the current one is accumulated.  All entries of one
-        // segment belong to one row B_k, so their columns (and positions) are distinct.
-        unsigned live = __ballot_sync(FULL, e > s);
-        int j = live ? __ffs(live) - 1 : -1;
-        live &= live - 1u;
-        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-        int64_t sj = 0;
-        int len = 0;
-        if (j >= 0) {
-          sj = __shfl_sync(FULL, s, j);
-          len = (int)(__shfl_sync(FULL, e, j) - sj);
-          const int32_t* cb = B.ci + sj;
-          const double* vb = B.v + sj;
-          if (lane < len) { c0 = __ldg(cb + lane); v0 = __ldg(vb + lane); }
-          if (lane + 32 < len) { c1 = __ldg(cb + lane + 32); v1 = __ldg(vb + lane + 32); }
-          if (lane + 64 < len) { c2 = __ldg(cb + lane + 64); v2 = __ldg(vb + lane + 64); }
-          if (lane + 96 < len) { c3 = __ldg(cb + lane + 96); v3 = __ldg(vb + lane + 96); }
-        }
-        while (j >= 0) {
-          const double aj = __shfl_sync(FULL, a, j);
-          const int jn = live ? __ffs(live) - 1 : -1;
+        // the non-empty segments of this batch of 32 k's (ballot), in lane order
+        unsigned live = __ballot_sync(FULL, len > 0);
+        if (!live) continue;
+        Quad qa, qb;
+        {
+          const int j = __ffs(live) - 1;
           live &= live - 1u;
-          int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-          double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
-          int64_t sn = 0;
-          int ln = 0;
-          if (jn >= 0) {
-            sn = __shfl_sync(FULL, s, jn);
-            ln = (int)(__shfl_sync(FULL, e, jn) - sn);
-            const int32_t* cb = B.ci + sn;
-            const double* vb = B.v + sn;
-            if (lane < ln) { n0 = __ldg(cb + lane); u0 = __ldg(vb + lane); }
-            if (lane + 32 < ln) { n1 = __ldg(cb + lane + 32); u1 = __ldg(vb + lane + 32); }
-            if (lane + 64 < ln) { n2 = __ldg(cb + lane + 64); u2 = __ldg(vb + lane + 64); }
-            if (lane + 96 < ln) { n3 = __ldg(cb + lane + 96); u3 = __ldg(vb + lane + 96); }
-          }
-          {
-            const int cc[4] = {c0, c1, c2, c3};
-            const double vv[4] = {v0, v1, v2, v3};
-            accumulate4(accw, bm, pre, b, aj, lane, len, c_lo, cc, vv);
-          }
-          if (len > 128) {
-            const int32_t* __restrict__ cb = B.ci + sj;
-            const double* __restrict__ vb = B.v + sj;
-            for (int q = 128 + lane; q < len; q += 128) {
-              const bool m1 = q + 32 < len, m2 = q + 64 < len, m3 = q + 96 < len;
-              const int d0 = __ldg(cb + q);
-              const double x0 = __ldg(vb + q);
-              int d1 = 0, d2 = 0, d3 = 0;
-              double x1 = 0.0, x2 = 0.0, x3 = 0.0;
-              if (m1) { d1 = __ldg(cb + q + 32); x1 = __ldg(vb + q + 32); }
-              if (m2) { d2 = __ldg(cb + q + 64); x2 = __ldg(vb + q + 64); }
-              if (m3) { d3 = __ldg(cb + q + 96); x3 = __ldg(vb + q + 96); }
-              const int cc[4] = {d0, d1, d2, d3};
-              const double vv[4] = {x0, x1, x2, x3};
-              accumulate4(accw, bm, pre, b, aj, lane, len - (q - lane), c_lo, cc, vv);
-            }
-          }
-          __syncwarp();
-          j = jn;
-          sj = sn;
-          len = ln;
-          c0 = n0; c1 = n1; c2 = n2; c3 = n3;
-          v0 = u0; v1 = u1; v2 = u2; v3 = u3;
+          qa.s = __shfl_sync(FULL, s, j);
+          qa.len = __shfl_sync(FULL, len, j);
+          qa.a = __shfl_sync(FULL, a, j);
+          load_quad(B, lane, qa);
         }
+        while (pipe_stage(B, accw, sink, bp, b, lane, c_lo, s, len, a, live, qa, qb) &&
+               pipe_stage(B, accw, sink, bp, b, lane, c_lo, s, len, a, live, qb, qa)) {
+        }
+        __syncwarp();
       }
     }
     if (members > 1) {
@@ -648,7 +657,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
       }
     }
   }
-  __syncthreads();  // every accumulation (and the k split's sum) is complete
+  __syncthreads();  // every accumulation (and the members' sum) is complete
   // 4. scaling (Taylor /i) and the fused beta D term (squaring +2T), in that order;
   //    a frozen row is a plain copy of D
   if (div != 1.0)
@@ -660,7 +669,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
     for (int64_t q = d0 + threadIdx.x; q < d1; q += T) {
       const int c = D.ci[q];
       if (upper && c < i) continue;
-      const int pos = (int)rank_of(bm, pre, c - b);
+      const int pos = (int)rank_of(bp, c - b);
       acc[pos] += coef * D.v[q];
     }
   }
@@ -670,7 +679,7 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
   //    off-diagonal entry stands for itself and its mirror in the sum of squares)
   double sq = 0.0;
   for (int k = threadIdx.x; k < cnt; k += T) {
-    const int col = b + column_at(bm, pre, W, k);
+    const int col = b + column_at(bp, W, k);
     ci_out[o0 + k] = col;
     if (k < lo_pos) continue;
     const double v = acc[k];
@@ -685,9 +694,9 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
   __syncthreads();
 }
 
-// Numeric pass.  Layout per row: an accumulator region (acc[cnt] doubles; before the
-// accumulation it holds wk[W], the prefix product counts), bm[W] words, pre[W] position
-// prefixes (16- or 32-bit).
+// Numeric pass.  Layout per row: an accumulator region (the members' accumulators of cacc
+// doubles each; before the accumulation it holds wk[W], the prefix product counts), then
+// bp[W], the bitmap words with their position prefixes.
 #ifndef SEXPM_NUMERIC_BLOCKS
 #define SEXPM_NUMERIC_BLOCKS 4
 #endif
@@ -702,6 +711,7 @@ __global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, C
   __shared__ unsigned ured[32];
   __shared__ double dred[32];
   __shared__ long long s_next;
+  __shared__ double sink[8];  // per-warp target of masked accumulator updates (never read back)
   unsigned char* mem = GLOBAL ? gscratch + (int64_t)blockIdx.x * gstride : smem;
   const int T = blockDim.x;
   const bool hasD = D.n > 0;
@@ -716,25 +726,19 @@ __global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, C
     const int cacc = upper ? cnt_up[i] : cnt;   // entries accumulated: positions cnt - cacc .. cnt
     double* acc = reinterpret_cast<double*>(mem) - (cnt - cacc);  // indexed by full-row position
     unsigned* wk = reinterpret_cast<unsigned*>(mem);
-    uint32_t* bm = reinterpret_cast<uint32_t*>(mem + acc_region(W, cnt, cacc, T >> 5, ks_bytes));
+    uint2* bp = reinterpret_cast<uint2*>(mem + acc_region(W, cnt, cacc, T >> 5, ks_bytes));
     for (int w = threadIdx.x; w < W; w += T) {
-      bm[w] = 0u;
+      bp[w].x = 0u;
       wk[w] = 0u;
     }
     if (row_diag && threadIdx.x == 0) row_diag[i] = 0.0;
     __syncthreads();
     // 1. pattern bitmap and products per word, from the word patterns
     const bool fz = frozen && frozen[i];
-    build_row_bitmap(A, WB, WD, hasD, i, b >> 5, bm, wk, upper, fz);
+    build_row_bitmap<2>(A, WB, WD, hasD, i, b >> 5, reinterpret_cast<uint32_t*>(bp), wk, upper, fz);
     __syncthreads();
-    if (small_prefix(cnt))
-      numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, cnt - cacc, acc, wk, bm,
-                  reinterpret_cast<unsigned short*>(bm + W), ci_out, v_out, row_sq, row_diag, ured, dred, work_total,
-                  ks_bytes);
-    else
-      numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, cnt - cacc, acc, wk, bm,
-                  reinterpret_cast<unsigned*>(bm + W),
-                  ci_out, v_out, row_sq, row_diag, ured, dred, work_total, ks_bytes);
+    numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, cnt - cacc, acc, wk, bp, &sink[threadIdx.x >> 5],
+                ci_out, v_out, row_sq, row_diag, ured, dred, work_total, ks_bytes);
     if (threadIdx.x == 0) s_next = nxt;
     __syncthreads();
     r = s_next;
