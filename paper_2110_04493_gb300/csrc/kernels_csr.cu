@@ -21,6 +21,14 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// |v| > t for finite v and t >= 0, decided on the bit patterns: non-negative doubles are
+// ordered as their bit patterns read as unsigned integers, so the test takes no FP64
+// instruction (the FP64 pipe is this GPU's scarce unit; the dropped sum of squares keeps it).
+__device__ __forceinline__ bool above(double v, unsigned long long tb) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull) > tb;
+}
+__device__ __forceinline__ unsigned long long bits_of(double t) { return (unsigned long long)__double_as_longlong(t); }
+
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 
@@ -86,12 +94,13 @@ __global__ void k_filter_pass(CsrD A, double t, int32_t* keep, double* part) {
   __shared__ double red[32];
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   double s = 0.0;
+  const unsigned long long tb = bits_of(t);
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
     const int64_t q0 = A.rp[i], q1 = A.rp[i + 1];
     int c = 0;
     for (int64_t q = q0 + lane_id(); q < q1; q += 32) {
       const double v = A.v[q];
-      if (fabs(v) > t) ++c; else s += v * v;
+      if (above(v, tb)) ++c; else s = fma(v, v, s);
     }
     c = warp_sum(c);
     if (lane_id() == 0) keep[i] = c;
@@ -196,6 +205,7 @@ __global__ void k_scan_apply(const int32_t* cnt, int64_t n, const int64_t* tile_
 __global__ void k_compact(CsrD A, double t, const int64_t* rp_out, int32_t* ci_out, double* v_out) {
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const unsigned lt = (1u << lane_id()) - 1u;
+  const unsigned long long tb = bits_of(t);
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
     const int64_t q0 = A.rp[i], q1 = A.rp[i + 1];
     int64_t o = rp_out[i];
@@ -203,7 +213,7 @@ __global__ void k_compact(CsrD A, double t, const int64_t* rp_out, int32_t* ci_o
       const int64_t q = qb + lane_id();
       const bool act = q < q1;
       const double v = act ? A.v[q] : 0.0;
-      const bool keep = act && fabs(v) > t;
+      const bool keep = act && above(v, tb);
       const unsigned m = __ballot_sync(FULL, keep);
       if (keep) {
         const int64_t d = o + __popc(m & lt);
@@ -307,25 +317,6 @@ __global__ void k_transpose_scatter(CsrD A, const int64_t* rp_t, int32_t* cursor
   }
 }
 
-__global__ void k_sort_rows(int64_t n, const int64_t* rp, int32_t* ci, double* v) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int64_t p0 = rp[i], p1 = rp[i + 1];
-  for (int64_t p = p0 + 1; p < p1; ++p) {
-    const int c = ci[p];
-    const double x = v[p];
-    int64_t q = p - 1;
-    while (q >= p0 && ci[q] > c) {
-      ci[q + 1] = ci[q];
-      v[q + 1] = v[q];
-      --q;
-    }
-    ci[q + 1] = c;
-    v[q + 1] = x;
-  }
-}
-
-
 // ---- batched (block-diagonal) helpers: inst[i] is the instance of row i; instances own
 //      contiguous row ranges seg[b] .. seg[b+1]
 
@@ -334,12 +325,12 @@ __global__ void k_sort_rows(int64_t n, const int64_t* rp, int32_t* ci, double* v
 __global__ void k_filter_pass_seg(CsrD A, const int32_t* inst, const double* t_inst, int32_t* keep, double* row_part) {
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
-    const double t = t_inst[inst[i]];
+    const unsigned long long tb = bits_of(t_inst[inst[i]]);
     int c = 0;
     double sq = 0.0;
     for (int64_t q = A.rp[i] + lane_id(); q < A.rp[i + 1]; q += 32) {
       const double v = A.v[q];
-      if (fabs(v) > t) ++c; else sq += v * v;
+      if (above(v, tb)) ++c; else sq = fma(v, v, sq);
     }
     c = warp_sum(c);
     sq = warp_sum(sq);
@@ -365,14 +356,14 @@ __global__ void k_compact_seg(CsrD A, const int32_t* inst, const double* t_inst,
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const unsigned lt = (1u << lane_id()) - 1u;
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
-    const double t = t_inst[inst[i]];
+    const unsigned long long tb = bits_of(t_inst[inst[i]]);
     const int64_t q0 = A.rp[i], q1 = A.rp[i + 1];
     int64_t o = rp_out[i];
     for (int64_t qb = q0; qb < q1; qb += 32) {
       const int64_t q = qb + lane_id();
       const bool act = q < q1;
       const double v = act ? A.v[q] : 0.0;
-      const bool keep = act && fabs(v) > t;
+      const bool keep = act && above(v, tb);
       const unsigned m = __ballot_sync(FULL, keep);
       if (keep) {
         const int64_t d = o + __popc(m & lt);

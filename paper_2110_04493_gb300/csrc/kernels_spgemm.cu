@@ -310,28 +310,60 @@ __global__ void k_classify(int64_t n, const int32_t* sched, const int32_t* words
 }
 
 // OR the word patterns of the rows B_k (k in A_i) and of D_i into the row bitmap bm
-// (word wlo of the row is bm[0]; word w at bm[w * STRIDE]).  When work != nullptr, work[w] also receives the number of
-// scalar products that land in word w (the popcount of every B_k mask ORed into it).
+// (word wlo of the row is bm[0]; word w at bm[w * STRIDE]).  When work != nullptr, work[w] also
+// receives the number of scalar products that land in word w (the popcount of every B_k mask
+// ORed into it); with upper set, only products at columns >= i are counted.
+// Each warp takes batches of 32 k's (one per lane: the k's a0 + 32 (w + nwarps m) + lane) and
+// streams the concatenation of their word patterns 32 entries at a time; lane l finds the k of
+// its entry by a binary search over the lanes' exclusive prefix of pattern lengths.  All
+// loads of a batch are independent (an OR does not depend on its order).
 // Block-wide; the caller synchronises afterwards.
-// With upper set, only products at columns >= i are counted as work.
 template <int STRIDE>
 __device__ __forceinline__ void build_row_bitmap(const CsrD& A, const WPat& WB, const WPat& WD, bool hasD, int64_t i,
                                                  int wlo, uint32_t* bm, unsigned* work, bool upper, bool fz) {
-  const int nwarps = blockDim.x >> 5;
+  const int nwarps = blockDim.x >> 5, lane = lane_id();
   const int64_t a0 = A.rp[i], a1 = fz ? a0 : A.rp[i + 1];
   const int iw = (int)(i >> 5);
   const uint32_t imask = ~((1u << (i & 31)) - 1u);
-  for (int64_t p = a0 + warp_id(); p < a1; p += nwarps) {
-    const int k = A.ci[p];
-    const int64_t e1 = WB.rp[k + 1];
-    for (int64_t e = WB.rp[k] + lane_id(); e < e1; e += 32) {
-      const int wa = WB.wi[e];
-      const int w = wa - wlo;
-      const uint32_t bits = WB.wb[e];
-      atomicOr(&bm[w * STRIDE], bits);
-      if (work) {
-        const uint32_t wbits = !upper || wa > iw ? bits : (wa == iw ? (bits & imask) : 0u);
-        if (wbits) atomicAdd(&work[w], (unsigned)__popc(wbits));
+  for (int64_t kb = a0 + 32 * warp_id(); kb < a1; kb += 32 * nwarps) {
+    int64_t e0 = 0;
+    int len = 0;
+    if (kb + lane < a1) {
+      const int k = A.ci[kb + lane];
+      e0 = WB.rp[k];
+      len = (int)(WB.rp[k + 1] - e0);
+    }
+    int excl = len;  // inclusive, then exclusive prefix of the lengths over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, excl, o);
+      if (lane >= o) excl += y;
+    }
+    const int total = __shfl_sync(FULL, excl, 31);
+    excl -= len;
+#pragma unroll 2
+    for (int f0 = 0; f0 < total; f0 += 32) {
+      const int f = f0 + lane;
+      // the last lane j with excl_j <= f holds f (lanes with an empty pattern share the
+      // prefix of the next lane, so the last such lane has a non-empty one)
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int ex = __shfl_sync(FULL, excl, j + step);
+        if (ex <= f) j += step;
+      }
+      const int64_t ej = __shfl_sync(FULL, e0, j);
+      const int xj = __shfl_sync(FULL, excl, j);
+      if (f < total) {
+        const int64_t e = ej + (f - xj);
+        const int wa = WB.wi[e];
+        const int w = wa - wlo;
+        const uint32_t bits = WB.wb[e];
+        atomicOr(&bm[w * STRIDE], bits);
+        if (work) {
+          const uint32_t wbits = !upper || wa > iw ? bits : (wa == iw ? (bits & imask) : 0u);
+          if (wbits) atomicAdd(&work[w], (unsigned)__popc(wbits));
+        }
       }
     }
   }
@@ -746,7 +778,7 @@ __global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, C
 }
 
 // Fills the entries below the diagonal of a structurally symmetric product whose upper part
-// (columns >= row) was computed: C[i][j] = C[j][i] for j < i, found by binary search in row j.
+// (columns >= row) was computed: C[i][j] = C[j][i] for j < i, found in row j.
 // One warp per row.  A partner that is absent (the pattern was not symmetric) counts a miss.
 __global__ void k_mirror(int64_t n, const int64_t* rp, const int32_t* ci, double* v, unsigned long long* misses) {
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -756,7 +788,11 @@ __global__ void k_mirror(int64_t n, const int64_t* rp, const int32_t* ci, double
       const int j = ci[p];
       if (j >= i) break;
       const int64_t q0 = rp[j], q1 = rp[j + 1];
-      const int64_t q = lower_bound_col(ci, q0, q1, (int)i);
+      // first probe: the point-mirrored index (rows that are translates of one symmetric
+      // offset set hold column i of row j at index cnt_j - 1 - t when column j sits at
+      // index t of row i), else binary search
+      int64_t q = q1 - 1 - (p - p0);
+      if (q < q0 || ci[q] != (int)i) q = lower_bound_col(ci, q0, q1, (int)i);
       if (q < q1 && ci[q] == (int)i) {
         v[p] = v[q];
       } else {

@@ -29,6 +29,14 @@
 namespace sexpm_noalloc {
 namespace {
 
+// |v| > t for finite v and t >= 0, decided on the bit patterns: non-negative doubles are
+// ordered as their bit patterns read as unsigned integers, so the test takes no FP64
+// instruction (the FP64 pipe is this GPU's scarce unit; the dropped sum of squares keeps it).
+__device__ __forceinline__ bool above(double v, unsigned long long tb) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull) > tb;
+}
+__device__ __forceinline__ unsigned long long bits_of(double t) { return (unsigned long long)__double_as_longlong(t); }
+
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int64_t kMaxRows = SEXPM_NOALLOC_MAX_ROWS;
 constexpr int kBlocks = 1024;      // fixed reduction grid: sums do not depend on timing
@@ -95,11 +103,12 @@ __global__ void k_pass(View A, double t, int32_t* keep, double* part) {
   __shared__ double red[32];
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   double s = 0.0;
+  const unsigned long long tb = bits_of(t);
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp(); i < A.n; i += nw) {
     int c = 0;
     for (int64_t q = A.rp[i] + lane(); q < A.rp[i + 1]; q += 32) {
       const double x = A.v[q];
-      if (fabs(x) > t) ++c; else s += x * x;
+      if (above(x, tb)) ++c; else s = fma(x, x, s);
     }
     c = wsum(c);
     if (lane() == 0) keep[i] = c;
@@ -177,13 +186,14 @@ __global__ void k_rows(const int32_t* cnt, int64_t n, const int64_t* tile, int64
 __global__ void k_keep(View A, double t, const int64_t* rp, int32_t* ci, double* v) {
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const unsigned lt = (1u << lane()) - 1u;
+  const unsigned long long tb = bits_of(t);
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp(); i < A.n; i += nw) {
     int64_t o = rp[i];
     for (int64_t qb = A.rp[i]; qb < A.rp[i + 1]; qb += 32) {
       const int64_t q = qb + lane();
       const bool act = q < A.rp[i + 1];
       const double x = act ? A.v[q] : 0.0;
-      const bool k = act && fabs(x) > t;
+      const bool k = act && above(x, tb);
       const unsigned m = __ballot_sync(FULL, k);
       if (k) {
         const int64_t d = o + __popc(m & lt);
