@@ -98,9 +98,15 @@ __global__ void k_filter_pass(CsrD A, double t, int32_t* keep, double* part) {
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
     const int64_t q0 = A.rp[i], q1 = A.rp[i + 1];
     int c = 0;
-    for (int64_t q = q0 + lane_id(); q < q1; q += 32) {
-      const double v = A.v[q];
-      if (above(v, tb)) ++c; else s = fma(v, v, s);
+    // four independent loads per lane and round (absent entries read as 0: dropped, adding 0)
+    for (int64_t q = q0 + lane_id(); q < q1; q += 128) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = q + 32 * u < q1 ? A.v[q + 32 * u] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (above(v[u], tb)) ++c; else s = fma(v[u], v[u], s);
+      }
     }
     c = warp_sum(c);
     if (lane_id() == 0) keep[i] = c;
@@ -209,18 +215,27 @@ __global__ void k_compact(CsrD A, double t, const int64_t* rp_out, int32_t* ci_o
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
     const int64_t q0 = A.rp[i], q1 = A.rp[i + 1];
     int64_t o = rp_out[i];
-    for (int64_t qb = q0; qb < q1; qb += 32) {
-      const int64_t q = qb + lane_id();
-      const bool act = q < q1;
-      const double v = act ? A.v[q] : 0.0;
-      const bool keep = act && above(v, tb);
-      const unsigned m = __ballot_sync(FULL, keep);
-      if (keep) {
-        const int64_t d = o + __popc(m & lt);
-        ci_out[d] = A.ci[q];
-        v_out[d] = v;
+    // four chunks of 32 per round: every load of the round is issued before the first store
+    for (int64_t qb = q0; qb < q1; qb += 128) {
+      double v[4];
+      int c[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t q = qb + 32 * u + lane_id();
+        v[u] = q < q1 ? A.v[q] : 0.0;
+        c[u] = q < q1 ? A.ci[q] : 0;
       }
-      o += __popc(m);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool keep = qb + 32 * u + lane_id() < q1 && above(v[u], tb);
+        const unsigned m = __ballot_sync(FULL, keep);
+        if (keep) {
+          const int64_t d = o + __popc(m & lt);
+          ci_out[d] = c[u];
+          v_out[d] = v[u];
+        }
+        o += __popc(m);
+      }
     }
   }
 }
@@ -359,18 +374,27 @@ __global__ void k_compact_seg(CsrD A, const int32_t* inst, const double* t_inst,
     const unsigned long long tb = bits_of(t_inst[inst[i]]);
     const int64_t q0 = A.rp[i], q1 = A.rp[i + 1];
     int64_t o = rp_out[i];
-    for (int64_t qb = q0; qb < q1; qb += 32) {
-      const int64_t q = qb + lane_id();
-      const bool act = q < q1;
-      const double v = act ? A.v[q] : 0.0;
-      const bool keep = act && above(v, tb);
-      const unsigned m = __ballot_sync(FULL, keep);
-      if (keep) {
-        const int64_t d = o + __popc(m & lt);
-        ci_out[d] = A.ci[q];
-        v_out[d] = v;
+    // four chunks of 32 per round: every load of the round is issued before the first store
+    for (int64_t qb = q0; qb < q1; qb += 128) {
+      double v[4];
+      int c[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t q = qb + 32 * u + lane_id();
+        v[u] = q < q1 ? A.v[q] : 0.0;
+        c[u] = q < q1 ? A.ci[q] : 0;
       }
-      o += __popc(m);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool keep = qb + 32 * u + lane_id() < q1 && above(v[u], tb);
+        const unsigned m = __ballot_sync(FULL, keep);
+        if (keep) {
+          const int64_t d = o + __popc(m & lt);
+          ci_out[d] = c[u];
+          v_out[d] = v[u];
+        }
+        o += __popc(m);
+      }
     }
   }
 }

@@ -66,20 +66,26 @@ __host__ __device__ __forceinline__ long long need_bytes(long long W, long long 
   return acc_bytes(W, cacc, q) + 8 * W;
 }
 
+// Resident 256-thread blocks per SM the numeric kernel is compiled for (its register budget).
+#ifndef SEXPM_NUMERIC_BLOCKS
+#define SEXPM_NUMERIC_BLOCKS 4
+#endif
+constexpr int kNumericWarpsPerSM = 8 * SEXPM_NUMERIC_BLOCKS;
+
 // Accumulation layout of a row: the block's warps form groups of `members` warps.  The
 // groups split the row's columns (equal shares of its products); the members of a group
 // split the k's of A_i (member q takes every members-th k) and accumulate into accumulator q
 // of their own; the members' accumulators are summed in member order.  members = 1 is a pure
 // column split (every warp searches each B_k for its columns); members = nwarps is a pure
 // k split (whole rows B_k, no search).  More members means fewer, longer segments and fewer
-// searches, at 8 bytes per accumulated entry and member.  The numeric kernel holds 32 warps
-// per SM (its register budget), so a block of nwarps warps may use nwarps/32 of the SM's
-// shared memory without lowering that occupancy: members is the largest power of two whose
-// row fits in that share of sm_bytes (sm_bytes = 0: column split).
+// searches, at 8 bytes per accumulated entry and member.  The numeric kernel holds
+// kNumericWarpsPerSM warps per SM (its register budget), so a block of nwarps warps may use
+// that fraction of the SM's shared memory without lowering the occupancy: members is the
+// largest power of two whose row fits in that share of sm_bytes (sm_bytes = 0: column split).
 constexpr int kKsplitBytesDefault = 220 << 10;
 __host__ __device__ __forceinline__ int ks_members(long long W, long long cnt, long long cacc, int nwarps,
                                                    int sm_bytes) {
-  const long long budget = (long long)sm_bytes * nwarps / 32;
+  const long long budget = (long long)sm_bytes * nwarps / kNumericWarpsPerSM;
   int q = nwarps;
   while (q > 1 && need_bytes(W, cnt, cacc, q) > budget) q >>= 1;
   return q;
@@ -500,6 +506,10 @@ __device__ void block_popc_prefix(uint2* bp, int W, unsigned* red) {
   __syncthreads();
 }
 
+// Rows of B up to this length are masked below the diagonal instead of searched (upper mode,
+// whole rows).
+constexpr int kMaskMax = 16;
+
 // One quad of a segment: up to 128 consecutive entries of one row B_k, entry 32 t + lane of
 // the quad in chunk t of this lane.  s is the quad's first entry, len the entries left in the
 // segment from s, a the factor A_ik.
@@ -648,9 +658,10 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
           int64_t e = b1;
           s = b0;
           if (groups == 1) {
-            // whole row; in the upper mode long rows start at the first column >= c_lo,
-            // short ones are masked entry by entry
-            if (upper && b1 - b0 > 64 && B.ci[b0] < c_lo) s = lower_bound_col(B.ci, b0, b1, c_lo);
+            // whole row; in the upper mode rows of more than kMaskMax entries start at the first
+            // column >= c_lo (a DFMA lane costs more than the search), shorter ones are masked
+            // entry by entry
+            if (upper && b1 - b0 > kMaskMax && B.ci[b0] < c_lo) s = lower_bound_col(B.ci, b0, b1, c_lo);
           } else if (b1 > b0) {
             const int f = B.ci[b0], l = B.ci[b1 - 1];
             if (f <= c_hi && l >= c_lo) {
@@ -729,9 +740,6 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
 // Numeric pass.  Layout per row: an accumulator region (the members' accumulators of cacc
 // doubles each; before the accumulation it holds wk[W], the prefix product counts), then
 // bp[W], the bitmap words with their position prefixes.
-#ifndef SEXPM_NUMERIC_BLOCKS
-#define SEXPM_NUMERIC_BLOCKS 4
-#endif
 template <bool GLOBAL>
 __global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, double beta, bool upper,
                           const uint8_t* frozen, const int32_t* cnt_up, const int32_t* rows,
