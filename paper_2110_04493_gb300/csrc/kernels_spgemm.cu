@@ -322,8 +322,12 @@ __global__ void k_classify(int64_t n, const int32_t* sched, const int32_t* words
 // Each warp takes batches of 32 k's (one per lane: the k's a0 + 32 (w + nwarps m) + lane) and
 // streams the concatenation of their word patterns 32 entries at a time; lane l finds the k of
 // its entry by a binary search over the lanes' exclusive prefix of pattern lengths.  All
-// loads of a batch are independent (an OR does not depend on its order).
+// loads of a batch are independent (an OR does not depend on its order).  Batches whose
+// patterns average kLongPattern entries or more are streamed one k at a time instead (the
+// search would cost more than the latency it hides).
 // Block-wide; the caller synchronises afterwards.
+constexpr int kLongPattern = 48;
+
 template <int STRIDE>
 __device__ __forceinline__ void build_row_bitmap(const CsrD& A, const WPat& WB, const WPat& WD, bool hasD, int64_t i,
                                                  int wlo, uint32_t* bm, unsigned* work, bool upper, bool fz) {
@@ -347,6 +351,24 @@ __device__ __forceinline__ void build_row_bitmap(const CsrD& A, const WPat& WB, 
     }
     const int total = __shfl_sync(FULL, excl, 31);
     excl -= len;
+    if (total >= 32 * kLongPattern) {
+      // long patterns (rows of B spread over many words): one k at a time, 32 entries a round
+      for (int j = 0; j < 32; ++j) {
+        const int64_t ej = __shfl_sync(FULL, e0, j);
+        const int lj = __shfl_sync(FULL, len, j);
+        for (int f = lane; f < lj; f += 32) {
+          const int wa = WB.wi[ej + f];
+          const int w = wa - wlo;
+          const uint32_t bits = WB.wb[ej + f];
+          atomicOr(&bm[w * STRIDE], bits);
+          if (work) {
+            const uint32_t wbits = !upper || wa > iw ? bits : (wa == iw ? (bits & imask) : 0u);
+            if (wbits) atomicAdd(&work[w], (unsigned)__popc(wbits));
+          }
+        }
+      }
+      continue;
+    }
 #pragma unroll 2
     for (int f0 = 0; f0 < total; f0 += 32) {
       const int f = f0 + lane;
