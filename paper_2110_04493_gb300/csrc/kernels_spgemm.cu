@@ -3,7 +3,9 @@
 // used for the Taylor terms S~_i = S^_{i-1} H_0 / i (Eq. 4.10) and the squaring
 // steps T~_i = 2 T^_{i-1} + T^_{i-1}^2 (Eq. 4.15).
 //
-// Row-wise (Gustavson) product, one thread block per output row.
+// Row-wise (Gustavson) product, one thread block per output row; each size class
+// of rows is one persistent launch of the resident blocks, which take rows from an
+// atomic counter in schedule order.
 //
 // Pattern.  The output pattern of row i is a bitmap over the row's column span
 // [base_i, hi_i] (base_i a multiple of 32).  B and D are first compressed to
@@ -13,16 +15,17 @@
 // atomicOr per (k, word) instead of one per scalar product.  The symbolic pass
 // counts the bits; the numeric pass rebuilds the bitmap the same cheap way.
 //
-// Values.  rank(c) = pre[c/32] + popc(bm[c/32] & below(c)) maps a column to
-// its position in the sorted output row, so the accumulator is a dense array
-// of exactly nnz(row) doubles already in column order.  The accumulator is
-// owner-computes: the row's positions are split into equal contiguous ranges,
-// one per warp; each warp visits every k of A_i, takes the part of B_k whose
-// columns fall inside its range (found by binary search), and updates its own
-// positions with a plain FMA (no atomics, one FP64 operation per product).
+// Values.  Each bitmap word is kept with its position prefix, and
+// rank(c) = prefix[c/32] + popc(mask[c/32] & below(c)) maps a column to its
+// position in the sorted output row, so an accumulator is a dense array of
+// exactly nnz(row) doubles already in column order.  The block's warps form
+// groups that split the row's columns (equal shares of its products); the
+// members of a group split the k's of A_i and accumulate the part of B_k inside
+// the group's columns into accumulators of their own, summed in member order.
+// Every product is one FP64 FMA on a shared-memory accumulator (no atomics).
 //
-// Rows are binned by the shared memory they need (bitmap, prefix counts and
-// accumulator); the widest rows use a per-block global-memory scratch slice.
+// Rows are binned by the shared memory they need (accumulators, bitmap words and
+// prefixes); the widest rows use a per-block global-memory scratch slice.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
