@@ -117,8 +117,21 @@ def _stream_ptr(stream=None) -> Optional[int]:
 
 # ------------------------------------------------------------------ views
 
+def _is_sparse_csr(H) -> bool:
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(H, torch.Tensor) and H.layout == torch.sparse_csr
+
+
 def _arrays(H) -> Tuple[Any, Any, Any, int]:
-    """Accepts (row_ptr, col, val[, n]) tuples or objects with row_ptr/col/val/n attributes."""
+    """Accepts a square 2-D torch.sparse_csr tensor, (row_ptr, col, val[, n]) tuples, or objects
+    with row_ptr/col/val/n attributes."""
+    if _is_sparse_csr(H):
+        if H.dim() != 2 or H.shape[0] != H.shape[1]:
+            raise ValueError("a square 2-D sparse CSR tensor is required")
+        return H.crow_indices(), H.col_indices(), H.values(), int(H.shape[0])
     if isinstance(H, (tuple, list)):
         rp, ci, v = H[0], H[1], H[2]
         n = H[3] if len(H) > 3 else len(rp) - 1
@@ -253,7 +266,8 @@ class Plan:
 
 
 def expm(H, tau: float = 1.0, eps: float = 1e-12, device="cuda", **opts):
-    """e^{tau H} as (row_ptr, col, val) torch tensors on `device`, plus the stats dict."""
+    """e^{tau H} as (row_ptr, col, val) torch tensors on `device`, plus the stats dict.  When H is
+    a torch.sparse_csr tensor, e^{tau H} is returned as one too (float64, int64 indices)."""
     plan = Plan(H, eps, **opts)
     try:
         res = plan.compute(tau)
@@ -264,6 +278,11 @@ def expm(H, tau: float = 1.0, eps: float = 1e-12, device="cuda", **opts):
             res.free()
     finally:
         plan.close()
+    if _is_sparse_csr(H):
+        import torch
+        rp, ci, v = out
+        n = rp.numel() - 1
+        out = torch.sparse_csr_tensor(rp, ci.to(torch.int64), v, size=(n, n))
     return out, st
 
 

@@ -87,3 +87,23 @@ def test_host_choose_MN_rejects_bad_input(lib):
         with pytest.raises(sexpm.SexpmError) as ei:
             sexpm.choose_MN(*bad)
         assert ei.value.code == -1
+
+
+def test_binding_marshals_a_torch_sparse_csr_tensor():
+    """A square torch.sparse_csr tensor is accepted as H: its crow/col/values become the CSR view
+    (int64 row pointers, int32 columns, float64 values); other layouts and shapes are rejected."""
+    torch = pytest.importorskip("torch")
+    import warnings
+    from paper_2110_04493_gb300 import sexpm
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        A = torch.tensor([[2.0, 0.0, 1.0], [0.0, 3.0, 0.0], [1.0, 0.0, 4.0]]).to_sparse_csr()
+        keep = []
+        view = sexpm._make_view(A, keep)
+        assert (view.n, view.nnz, view.on_device) == (3, 5, 0)
+        rp, ci, v = keep
+        assert rp.dtype == torch.int64 and ci.dtype == torch.int32 and v.dtype == torch.float64
+        assert rp.tolist() == [0, 2, 3, 5] and ci.tolist() == [0, 2, 1, 0, 2]
+        assert v.tolist() == [2.0, 1.0, 3.0, 1.0, 4.0]
+        with pytest.raises(ValueError):
+            sexpm._arrays(torch.ones(2, 3).to_sparse_csr())

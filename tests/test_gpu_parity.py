@@ -269,3 +269,23 @@ def test_accumulation_modes_match_oracle(sx, monkeypatch, ks_bytes):
     H = dirichlet_laplacian(40, 2)
     _check_method(sx, H, 2.253 / 41 ** 2, 1e-12, symmetric=1)
     _check_method(sx, H, 2.253 / 41 ** 2, 1e-12, symmetric=0)
+
+
+def test_expm_takes_and_returns_torch_sparse_csr(sx):
+    """sexpm.expm on a torch.sparse_csr tensor returns e^{tau H} as one, identical to the result
+    of the (row_ptr, col, val) path."""
+    import warnings
+    import torch
+    H = dirichlet_laplacian(16, 2)
+    tau = 2.253 / 17 ** 2
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        Hs = torch.sparse_csr_tensor(torch.from_numpy(H.row_ptr.astype(np.int64)),
+                                     torch.from_numpy(H.col.astype(np.int64)),
+                                     torch.from_numpy(H.val.astype(np.float64)), size=(H.n, H.n)).cuda()
+        E, st = sx.expm(Hs, tau, 1e-12)
+        assert E.layout == torch.sparse_csr and tuple(E.shape) == (H.n, H.n)
+        (rp, ci, v), _ = sx.expm(torch_csr(H), tau, 1e-12)
+        assert torch.equal(E.crow_indices().cpu(), rp.cpu())
+        assert torch.equal(E.col_indices().cpu(), ci.cpu().to(torch.int64))
+        assert torch.equal(E.values().cpu(), v.cpu())
