@@ -83,6 +83,18 @@ void Pool::release(void* p, size_t bytes, cudaStream_t s) {
   g_live.fetch_sub((int64_t)bytes);
 }
 
+int current_device() {
+  int dev = 0;
+  SX_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) fail(SEXPM_ECUDA, "device ordinal out of range");
+  return dev;
+}
+
+std::mutex& device_setup_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t k) { g_launches.fetch_add(k); }
 int64_t launches() { return g_launches.load(); }

@@ -234,11 +234,10 @@ void sddmm(const CsrD& P, const CsrD& A, const CsrD& B, double alpha, double bet
            cudaStream_t s, HostScalars& hs) {
   const int64_t n = P.n;
   if (n == 0 || P.nnz == 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static bool attr[64] = {};
+  once_per_device(attr, [] {
     SX_CUDA(cudaFuncSetAttribute(k_sddmm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kSddmmMaxWords));
-    attr = true;
-  }
+  });
   DevBuf<int32_t> base(n, s), words(n, s);
   DevBuf<unsigned> maxw(1, s);
   SX_CUDA(cudaMemsetAsync(maxw.p, 0, sizeof(unsigned), s));

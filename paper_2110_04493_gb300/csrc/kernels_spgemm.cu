@@ -882,13 +882,14 @@ int64_t resident_blocks(K kernel, int threads, int bytes) {
   return (int64_t)std::max(per_sm, 1) * num_sms();
 }
 
+// Dynamic shared-memory limit of the row kernels, once per device.
 void set_smem_limits() {
-  static bool done = false;
-  if (done) return;
-  const int cap = kClassBytes[kClasses - 2];
-  SX_CUDA(cudaFuncSetAttribute(k_symbolic<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-  SX_CUDA(cudaFuncSetAttribute(k_numeric<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-  done = true;
+  static bool done[64] = {};
+  once_per_device(done, [] {
+    const int cap = kClassBytes[kClasses - 2];
+    SX_CUDA(cudaFuncSetAttribute(k_symbolic<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    SX_CUDA(cudaFuncSetAttribute(k_numeric<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  });
 }
 
 struct EventPair {

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <mutex>
 #include <stdint.h>
 
 #include <string>
@@ -103,6 +105,19 @@ struct HostScalars {
 };
 
 // Number of kernels this library has enqueued (all launchers add to it).
+// Runs set() once per CUDA device for this flag set (the current device; devices 0..63), for
+// per-device settings such as a kernel's shared-memory limit (cudaFuncSetAttribute applies to
+// the current device only).  Thread-safe; a device counts as done only once set() returned.
+int current_device();
+std::mutex& device_setup_mutex();
+template <typename F>
+void once_per_device(bool (&done)[64], F set) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(device_setup_mutex());
+  if (done[dev]) return;
+  set();
+  done[dev] = true;
+}
 void count_launches(int64_t k);
 int64_t launches();
 
