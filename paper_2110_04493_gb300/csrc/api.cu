@@ -401,17 +401,26 @@ struct Record {
 };
 
 // One filtered incremental squaring T^_k = filter(2 T^_{k-1} + T^_{k-1}^2) (Eq. 4.15 with the
-// threshold of reading 8); deterministic, so a replay reproduces the forward exactly.
+// threshold of reading 8); deterministic, so a replay reproduces the forward exactly.  When
+// drop_input is given (the owner of T), it is released as soon as the product has been formed
+// (stream-ordered), so that T^_{k-1} is not held while the unfiltered T~_k is filtered.
 void square_step(const sexpm_options& o, const CsrD& T, int k, double a, double r0, bool sym, cudaStream_t s,
-                 HostScalars& hs, RowStats& rs, CsrOwned& Tn, sexpm_step_stats* rec, const int32_t* sched) {
+                 HostScalars& hs, RowStats& rs, CsrOwned& Tn, sexpm_step_stats* rec, const int32_t* sched,
+                 CsrOwned* drop_input = nullptr) {
   Timer ts(s);
   const int64_t n = T.n;
+  const int64_t nnz_in = T.nnz;
   const double ri = std::ldexp(r0, k);
   CsrOwned Tt;
   SpgemmTimes tm;
   int64_t done = 0;
   const int64_t prod = spgemm(T, T, T, 1.0, 2.0, s, Tt, &rs, hs, &tm, sym, &done, nullptr, sched);
-  const double flops = 2.0 * (double)done + 2.0 * (double)T.nnz;
+  if (drop_input) {
+    drop_input->rp.free();
+    drop_input->ci.free();
+    drop_input->v.free();
+  }
+  const double flops = 2.0 * (double)done + 2.0 * (double)nnz_in;
   double normF = 1.0;
   if (o.square_scale) {
     const double sq = reduce_sum(rs.sq.p, n, s, hs);
@@ -583,7 +592,7 @@ void compute_impl(sexpm_plan_t* p, double tau, sexpm_result* res, Record* record
   for (int i = 1; i <= N; ++i) {
     CsrOwned Tn;
     sexpm_step_stats rec;
-    square_step(o, T.view(), i, a, r0, sym, s, hs, rs, Tn, &rec, p->sched.p);
+    square_step(o, T.view(), i, a, r0, sym, s, hs, rs, Tn, &rec, p->sched.p, &T);
     T = std::move(Tn);
     res->steps.push_back(rec);
     if (record && (i % record->stride == 0 || i == N)) copy_csr(T.view(), s, record->T[i]);
