@@ -26,6 +26,14 @@
  *     legacy default stream).  Calls synchronise that stream before they
  *     return, because the method reads scalar reductions back to the host
  *     between kernels (Algorithm 4.1 is a host-driven iteration).
+ *   - Results are reproducible run to run: every sum has an order fixed by
+ *     the input and the launch shapes.
+ *
+ * Environment (tuning only; results change at most by rounding):
+ *   SEXPM_KSPLIT_BYTES  per-SM shared-memory budget (bytes) under which a sparse
+ *                       product row gives its warps private accumulators and
+ *                       splits the k's of A_i among them (default 225280; 0 =
+ *                       every warp owns a column range).  Read at every product.
  */
 #ifndef SEXPM_H_
 #define SEXPM_H_
