@@ -3,7 +3,8 @@
 Argument marshalling only: every step of the method runs inside the library's
 CUDA kernels.  PyTorch supplies device buffers and the current CUDA stream.
 The library must have been built (``python -m paper_2110_04493_gb300.build``);
-importing the binding without it raises immediately: there is no CPU fallback.
+without it the first call into the library raises ImportError: there is no CPU
+fallback.
 """
 from __future__ import annotations
 
