@@ -7,6 +7,7 @@ import math
 import os
 import re
 
+import numpy as np
 import pytest
 
 from oracle import sexpm_oracle as O
@@ -107,3 +108,18 @@ def test_binding_marshals_a_torch_sparse_csr_tensor():
         assert v.tolist() == [2.0, 1.0, 3.0, 1.0, 4.0]
         with pytest.raises(ValueError):
             sexpm._arrays(torch.ones(2, 3).to_sparse_csr())
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with libsexpm.so absent, every entry into the method raises ImportError."""
+    from paper_2110_04493_gb300 import sexpm
+    monkeypatch.setattr(sexpm, "_lib", None)
+    monkeypatch.setattr(sexpm, "LIB_PATH", str(tmp_path / "libsexpm.so"))
+    with pytest.raises(ImportError):
+        sexpm.load()
+    with pytest.raises(ImportError):
+        sexpm.rho(10, 0.5)
+    # the method itself: ImportError for the library, or the CUDA runtime's own error first on a
+    # machine without a GPU; never a result
+    with pytest.raises((ImportError, RuntimeError)):
+        sexpm.expm((np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([1.0]), 1), 1.0, 1e-12)
