@@ -358,3 +358,46 @@ def test_pins_catch_keeping_the_dropped_side(monkeypatch):
     H = toeplitz_trid(2000, 1.0, -2.0, 1.0).to_scipy()
     E, st, tr = O.expm(H, 1.0, 1e-16, keep=True)
     assert [O.bandwidth(T) for T in tr["T"][1:]] != golden("table3_squaring_bandwidths.txt")["lambda"]
+
+
+# ---------------------------------------------------------------- Algorithm 4.1, streamed form
+
+def _alg41_streamed(kept, tail_sq, eps_g, e_r, max_iter=100):
+    """Algorithm 4.1 on the entries above L plus tail_sq, the sum of squares of the entries at or
+    below L (dropped by every pass).  Returns (eps_f, passes, b, smallest eps_f visited)."""
+    stash = np.abs(np.asarray(kept, dtype=np.float64))
+    m, b, n, eps_f, lowest = 1.0, math.inf, 0, eps_g, math.inf
+    while b > eps_g * (1.0 + e_r):
+        assert n < max_iter
+        eps_f = eps_g / m
+        lowest = min(lowest, eps_f)
+        stash = stash[stash <= eps_f]
+        b = math.sqrt(tail_sq + float(np.sum(stash * stash)))
+        m = b / eps_f
+        n += 1
+    return eps_f, n, b, lowest
+
+
+def test_alg41_thresholds_are_bounded_below_so_it_streams_exactly():
+    """Every threshold of Algorithm 4.1 is >= eps_g / sqrt(nnz): t_0 = eps_g, and the dropped
+    part at t_j has F-norm b_j <= sqrt(nnz) t_j, so t_{j+1} = eps_g t_j / b_j >= eps_g / sqrt(nnz).
+    Entries at or below L = eps_g / sqrt(nnz) are therefore dropped by every pass, and the filter
+    run on the other entries plus their sum of squares visits the same thresholds and keeps the
+    same entries as the filter on all of them (the form a chunked product can stream)."""
+    rng = np.random.default_rng(7)
+    streamed_some = 0
+    for _ in range(60):
+        nnz = int(rng.integers(1, 4000))
+        v = rng.standard_normal(nnz) * np.exp(rng.uniform(-45.0, 0.0, nnz))
+        eps_g = float(np.exp(rng.uniform(-35.0, -2.0)))
+        t, passes, b = O.alg41_threshold(v, eps_g, 0.1)
+        L = eps_g / math.sqrt(nnz)
+        low = np.abs(v) <= L
+        streamed_some += int(low.any())
+        t2, passes2, b2, lowest = _alg41_streamed(v[~low], float(np.sum(v[low] ** 2)), eps_g, 0.1)
+        assert lowest >= L
+        assert passes2 == passes
+        assert t2 == pytest.approx(t, rel=1e-12)
+        assert b2 == pytest.approx(b, rel=1e-12, abs=1e-300)
+        assert np.array_equal(np.abs(v) > t, np.abs(v) > t2)
+    assert streamed_some > 30
