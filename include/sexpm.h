@@ -192,7 +192,7 @@ int sexpm_choose_MN(double norm_H, double eps, int32_t n_extra, int32_t max_M, i
 /* Many independent matrices H_b (b = 0..count-1, sizes may differ) planned together: the
  * instances are stored as one block-diagonal matrix, so every step of Algorithm 4.2 runs as one
  * set of kernel launches for the whole batch.  Validation, symmetry and normality are per
- * instance.  eps is shared.  Not in the paper (the benchmark spec's batched form of Algorithm 4.2). */
+ * instance.  eps is shared.  Not in the paper (a batched form of Algorithm 4.2). */
 int sexpm_plan_batched(const sexpm_csr_view* Hs, int32_t count, double eps, const sexpm_options* opt,
                        void* stream, sexpm_plan_t** out);
 
@@ -216,7 +216,7 @@ int sexpm_compute_batched(sexpm_plan_t* plan, const double* taus, sexpm_result_t
  * squarings (0: ceil(sqrt(N))) and the iterates in between are recomputed in the reverse pass.
  * *dH receives a result with the pattern of H (its stats are those of the forward run);
  * if expm_out is not NULL it receives e^{tau H} of that forward run.  Not in the paper
- * (the benchmark spec's differentiation form). */
+ * (the differentiation form of the method). */
 int sexpm_adjoint(sexpm_plan_t* plan, double tau, const sexpm_csr_view* W, int32_t ckpt_stride,
                   sexpm_result_t** dH, sexpm_result_t** expm_out);
 
