@@ -177,6 +177,10 @@ int64_t sexpm_kernel_launches(void);
  * the driver (the pool keeps freed blocks for reuse otherwise). */
 int sexpm_release_memory(void);
 
+/* Bytes the library currently holds from its device pool (all devices) and the largest
+ * value since the last sexpm_compute started (or since load).  Either pointer may be NULL. */
+int sexpm_pool_stats(int64_t* live_bytes, int64_t* peak_bytes);
+
 /* Host-only helpers (no GPU needed): the scalar choices of Algorithm 4.2. */
 
 /* Eq. (4.5): (1/M!) sum_k x^{M+1+k} / (k! (M+1+k)). */
@@ -253,15 +257,18 @@ int sexpm_filter(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_
  * A must be a device CSR (on_device = 1) with at most SEXPM_NOALLOC_MAX_ROWS rows (larger
  * inputs return SEXPM_EOVERFLOW with a message).  The caller provides the outputs on the
  * device: out_row_ptr (n+1 entries) and out_col / out_val with room for out_capacity
- * entries (nnz(A) always suffices; if the kept part is larger, SEXPM_EOVERFLOW).  On success
- * *nnz_out is the number of kept entries and t, iters and b are as for sexpm_filter.
+ * entries (nnz(A) always suffices; if the kept part is larger, SEXPM_EOVERFLOW and none of
+ * the three output arrays is written).  On success *nnz_out is the number of kept entries
+ * and t, iters and b are as for sexpm_filter.
  *
  * Scratch (per-row kept counts, per-block partial sums, scan tile sums; about 4.2 MB) lives
  * in one static device array that every GPU loading the library holds until the process
  * exits.  The first call on a device looks up its address (cudaGetSymbolAddress, once per
- * device); make that first call before any stream capture.  All calls share the array:
- * calls that overlap on the GPU race on it, so the caller must serialise them.  The call
- * synchronises `stream` before it returns. */
+ * device); make that first call before any stream capture.  The address stays cached for
+ * the process: after a cudaDeviceReset of a device, do not call this entry point on it
+ * again.  `stream` must belong to the current device (SEXPM_EINVAL otherwise).  All calls
+ * share the array: calls that overlap on the GPU race on it, so the caller must serialise
+ * them.  The call synchronises `stream` before it returns. */
 int sexpm_filter_noalloc(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_iters, void* stream,
                          int64_t* out_row_ptr, int32_t* out_col, double* out_val, int64_t out_capacity,
                          int64_t* nnz_out, double* t, int32_t* iters, double* b);

@@ -647,6 +647,12 @@ int sexpm_release_memory(void) {
   SX_API_END
 }
 
+int sexpm_pool_stats(int64_t* live_bytes, int64_t* peak_bytes) {
+  if (live_bytes) *live_bytes = Pool::live();
+  if (peak_bytes) *peak_bytes = Pool::peak();
+  return SEXPM_OK;
+}
+
 int sexpm_options_default(sexpm_options* opt) {
   if (!opt) return SEXPM_EINVAL;
   opt->e_r = 0.1;

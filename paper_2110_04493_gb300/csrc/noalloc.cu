@@ -12,9 +12,12 @@
 //
 // The first call on a device looks up the array's device address with
 // cudaGetSymbolAddress (once per device, with that device current); make that first
-// call before any stream capture.  Every call shares the array, so calls that overlap on
-// the GPU (different streams, different host threads) race on it and must be serialised
-// by the caller.
+// call before any stream capture.  The address is cached for the life of the process:
+// after a cudaDeviceReset the cache is stale, so a caller that resets a device must not
+// call this entry point on that device again.  `stream` must belong to the current
+// device (checked).  Every call shares the array, so calls that overlap on the GPU
+// (different streams, different host threads) race on it and must be serialised by the
+// caller.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -255,6 +258,15 @@ int run(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_iters, vo
   int rc = scratch_for_current_device(&base);
   if (rc != SEXPM_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    // the cached scratch address is the current device's: the stream must run there too
+    int dev = 0, sdev = 0;
+    NA_CUDA(cudaGetDevice(&dev));
+    NA_CUDA(cudaStreamGetDevice(s, &sdev));
+    if (sdev != dev)
+      return err(SEXPM_EINVAL, "the stream belongs to device " + std::to_string(sdev) + ", the current device is " +
+                                   std::to_string(dev));
+  }
   const View V{A->n, A->nnz, A->row_ptr, A->col, A->val};
   int32_t* keep = reinterpret_cast<int32_t*>(base + kOffKeep);
   double* part = reinterpret_cast<double*>(base + kOffPart);
@@ -295,17 +307,19 @@ int run(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_iters, vo
     m = b / eps_f;
     ++it;
   }
-  // row pointers of the kept part, then the compaction
+  // kept total first (tile sums and their scan live in the scratch array), so that nothing of
+  // the caller's outputs is written when they are too small; then row pointers and compaction
   const int64_t tiles = (n + kScanTile - 1) / kScanTile;
   k_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(keep, n, tile);
   k_tile_scan<<<1, 32, 0, s>>>(tile, tiles);
-  k_rows<<<(unsigned)tiles, kScanThreads, 0, s>>>(keep, n, tile, out_row_ptr);
   NA_CUDA(cudaGetLastError());
   int64_t kept = 0;
   NA_CUDA(cudaMemcpyAsync(&kept, tile + tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   NA_CUDA(cudaStreamSynchronize(s));
   if (kept > out_capacity)
     return err(SEXPM_EOVERFLOW, "kept " + std::to_string(kept) + " entries but the output holds " + std::to_string(out_capacity));
+  k_rows<<<(unsigned)tiles, kScanThreads, 0, s>>>(keep, n, tile, out_row_ptr);
+  NA_CUDA(cudaGetLastError());
   if (kept > 0) {
     k_keep<<<kBlocks, kThreads, 0, s>>>(V, eps_f, out_row_ptr, out_col, out_val);
     NA_CUDA(cudaGetLastError());

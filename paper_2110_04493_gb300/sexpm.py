@@ -86,6 +86,7 @@ def load() -> ctypes.CDLL:
     L.sexpm_kernel_launches.restype = ctypes.c_int64
     L.sexpm_kernel_launches.argtypes = []
     L.sexpm_release_memory.argtypes = []
+    L.sexpm_pool_stats.argtypes = [P(ctypes.c_int64), P(ctypes.c_int64)]
     L.sexpm_rho.argtypes = [ctypes.c_int32, ctypes.c_double]
     L.sexpm_rho.restype = ctypes.c_double
     L.sexpm_choose_MN.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
@@ -425,6 +426,13 @@ def kernel_launches() -> int:
 def release_memory() -> None:
     """Return the library's cached device memory to the driver."""
     _check(load().sexpm_release_memory())
+
+
+def pool_stats() -> Tuple[int, int]:
+    """(live, peak) bytes the library holds from its device pool (sexpm_pool_stats)."""
+    live, peak = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().sexpm_pool_stats(ctypes.byref(live), ctypes.byref(peak)))
+    return live.value, peak.value
 
 
 def rho(M: int, x: float) -> float:
