@@ -85,6 +85,13 @@ typedef struct {
                                the sparse products visit the rows in strips of 32 consecutive x for
                                cache locality (the results do not depend on the order); 0: natural
                                row order */
+  int64_t chunk_bytes;      /* squaring steps whose unfiltered product T~_i would not fit in free
+                               device memory are formed in row chunks and filtered exactly as the
+                               whole (Algorithm 4.1 streamed: every threshold it visits is at least
+                               eps_g / sqrt(nnz(T~_i)), so a chunk keeps only its entries above that
+                               bound and the sum of squares of the rest).  0 (default): chunk only
+                               when needed, chunks sized from free memory; > 0: chunks of at most
+                               this many bytes of T~_i whenever T~_i is larger. */
 } sexpm_options;
 
 typedef struct sexpm_plan sexpm_plan_t;
@@ -95,7 +102,7 @@ typedef struct {
   int32_t phase;      /* 0 = Taylor term S^_i, 1 = squaring step T^_i */
   int32_t i;
   int32_t iters;      /* Algorithm 4.1 passes */
-  int32_t pad_;
+  int32_t chunks;     /* row chunks the product was formed in (1: whole) */
   double eps_g;       /* bound on the F-norm of the dropped part */
   double t;           /* final eps_f: stored entries with |v| <= t were dropped */
   double b;           /* F-norm of the dropped part */
@@ -110,6 +117,9 @@ typedef struct {
   double ms_filter;   /* Algorithm 4.1 passes, row-pointer scan and compaction */
   double flops;       /* FP64 operations of the numeric pass: 2 products_done + the fused term */
   double bytes_filter;/* algorithmic bytes moved by the filter passes, scan and compaction */
+  int64_t nnz_stream; /* chunked steps: entries kept by the streaming bound (Algorithm 4.1's input) */
+  int64_t rows_class[6]; /* rows of the numeric pass per size class (shared memory 8, 24, 56, 112,
+                            220 KB; the last class accumulates in global memory) */
 } sexpm_step_stats;
 
 typedef struct {
@@ -223,6 +233,22 @@ int sexpm_compute_batched(sexpm_plan_t* plan, const double* taus, sexpm_result_t
  * (the differentiation form of the method). */
 int sexpm_adjoint(sexpm_plan_t* plan, double tau, const sexpm_csr_view* W, int32_t ckpt_stride,
                   sexpm_result_t** dH, sexpm_result_t** expm_out);
+
+/* The forward half of sexpm_adjoint, for callers that differentiate later (an autograd
+ * function's forward and backward): computes e^{tau H} with every product formed, keeping
+ * H_0, the filtered Taylor terms and T^_k at the checkpoints k = 0, ckpt_stride, 2 ckpt_stride,
+ * .., N (0: ceil(sqrt(N))) in *tape, which owns that device memory and borrows the plan (the
+ * plan must outlive the tape).  *expm_out (may be NULL) receives e^{tau H}.  Not in the paper. */
+typedef struct sexpm_tape sexpm_tape_t;
+int sexpm_forward_keep(sexpm_plan_t* plan, double tau, int32_t ckpt_stride, sexpm_result_t** expm_out,
+                       sexpm_tape_t** tape);
+
+/* The reverse half: dL/dH on the stored pattern of H for W = dL/dE, from a kept forward (the
+ * iterates between checkpoints are recomputed).  A tape may serve several calls.  Same result
+ * as sexpm_adjoint with the same tau and ckpt_stride. */
+int sexpm_adjoint_tape(sexpm_tape_t* tape, const sexpm_csr_view* W, sexpm_result_t** dH);
+
+void sexpm_tape_free(sexpm_tape_t* tape);
 
 /* ------------------------------------------------------------ step calls */
 /* The individual steps of the hot path on caller-provided device CSR views,

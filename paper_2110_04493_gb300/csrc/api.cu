@@ -11,6 +11,7 @@
 // the host exactly as the algorithm states.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -172,37 +173,61 @@ struct FilterOut {
   double bytes = 0.0;
 };
 
-// Algorithm 4.1 on the stored values of A, then A~ = A - b_n into `out`.
-FilterOut filter_alg41(const CsrD& A, double eps_g, double e_r, int max_iters, cudaStream_t s, CsrOwned& out,
-                       HostScalars& hs) {
+// Algorithm 4.1 on the stored values of the row pieces P (together rows 0..n-1, in order), then
+// A~ = A - b_n into `out`.  `extra` is the sum of squares of entries dropped before (by the exact
+// streaming bound, below every threshold the algorithm visits): it joins every pass's sum.
+// Each pass streams the values once and records per-tile kept counts; the compaction after the
+// last pass uses the counts of that pass.
+FilterOut filter_alg41_pieces(const std::vector<Piece>& P, int64_t n, double extra, double eps_g, double e_r,
+                              int max_iters, cudaStream_t s, CsrOwned& out, HostScalars& hs) {
   FilterOut r;
   Timer tf(s);
-  DevBuf<int32_t> keep(A.n ? A.n : 1, s);
+  std::vector<int64_t> tile_base(P.size() + 1, 0);
+  int64_t nnz_all = 0;
+  for (size_t p = 0; p < P.size(); ++p) {
+    tile_base[p + 1] = tile_base[p] + tiles_of(P[p].nnz);
+    nnz_all += P[p].nnz;
+  }
+  const int64_t T = tile_base.back();
+  DevBuf<int32_t> tcnt(T ? T : 1, s);
   double m = 1.0;
   double b = std::numeric_limits<double>::infinity();  // the first pass always runs
   double eps_f = eps_g;
-  int n = 0;
+  int it = 0;
   while (b > eps_g * (1.0 + e_r)) {
-    if (n >= max_iters) fail(SEXPM_ENOCONV, "Algorithm 4.1 did not converge within " + std::to_string(max_iters) + " passes");
+    if (it >= max_iters) fail(SEXPM_ENOCONV, "Algorithm 4.1 did not converge within " + std::to_string(max_iters) + " passes");
     eps_f = eps_g / m;
-    b = std::sqrt(filter_pass(A, eps_f, keep.p, s, hs));
+    b = std::sqrt(pass_pieces(P, tile_base, eps_f, tcnt.p, s, hs) + extra);
     m = b / eps_f;
-    ++n;
+    ++it;
   }
-  out.n = A.n;
-  out.rp.reset(A.n + 1, s);
-  out.nnz = scan_counts(keep.p, A.n, out.rp.p, s, hs);
+  out.n = n;
+  out.rp.reset(n + 1, s);
+  DevBuf<int64_t> toff(T + 1, s);
+  out.nnz = scan_counts(tcnt.p, T, toff.p, s, hs);
   out.ci.reset(out.nnz, s);
   out.v.reset(out.nnz, s);
-  compact(A, eps_f, out, s);
+  if (n == 0) SX_CUDA(cudaMemsetAsync(out.rp.p, 0, sizeof(int64_t), s));
+  else compact_pieces(P, tile_base, eps_f, toff.p, n, out, s);
   r.t = eps_f;
   r.b = b;
-  r.iters = n;
+  r.iters = it;
   r.ms = tf.ms();
-  const double nr = (double)A.n + 1.0;
-  r.bytes = n * (8.0 * A.nnz + 8.0 * nr + 4.0 * A.n) + (4.0 * A.n + 8.0 * nr) +
-            (12.0 * A.nnz + 16.0 * nr + 12.0 * out.nnz);
+  r.bytes = it * 8.0 * nnz_all + 12.0 * nnz_all + 12.0 * out.nnz + 16.0 * ((double)n + 1.0);
   return r;
+}
+
+// Algorithm 4.1 on one whole matrix.
+FilterOut filter_alg41(const CsrD& A, double eps_g, double e_r, int max_iters, cudaStream_t s, CsrOwned& out,
+                       HostScalars& hs) {
+  Piece p;
+  p.r0 = 0;
+  p.r1 = A.n;
+  p.nnz = A.nnz;
+  p.rp = A.rp;
+  p.ci = A.ci;
+  p.v = A.v;
+  return filter_alg41_pieces(std::vector<Piece>{p}, A.n, 0.0, eps_g, e_r, max_iters, s, out, hs);
 }
 
 void copy_csr(const CsrD& A, cudaStream_t s, CsrOwned& out) {
@@ -400,10 +425,52 @@ struct Record {
   double tau = 0.0, a = 0.0, r0 = 0.0;
 };
 
+// A forward run kept for its reverse pass (sexpm_forward_keep).  The plan is borrowed.
+struct sexpm_tape {
+  sexpm_plan_t* plan = nullptr;
+  double tau = 0.0;
+  Record rec;
+  sexpm_stats_t st;
+  std::vector<sexpm_step_stats> steps;
+};
+
+// Device bytes the library can still allocate: free device memory plus what its pool holds
+// unused.
+int64_t device_available_bytes() {
+  size_t fr = 0, tot = 0;
+  SX_CUDA(cudaMemGetInfo(&fr, &tot));
+  uint64_t reserved = 0, used = 0;
+  cudaMemPool_t pool = pool_for_current_device();
+  SX_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+  SX_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  return (int64_t)fr + (int64_t)(reserved > used ? reserved - used : 0);
+}
+
+// Bytes of the unfiltered product one chunk may hold, or 0 when the product is formed whole.
+// Whole: the product T~ (12 B per entry) and, in the worst case, a filtered copy of the same
+// size must fit, with T^_{k-1} released after the product.  Otherwise chunks of an eighth of
+// what is free (at least 256 MB) leave room for the kept pieces and the result.
+int64_t chunk_limit(const sexpm_options& o, int64_t raw_entries, int64_t in_bytes, bool releases_input) {
+  const int64_t raw = 12 * raw_entries;
+  if (o.chunk_bytes > 0) return raw > o.chunk_bytes ? o.chunk_bytes : 0;
+  const int64_t avail = device_available_bytes();
+  const int64_t margin = (int64_t)2 << 30;
+  if (raw + margin <= avail && 2 * raw + margin <= avail + (releases_input ? in_bytes : 0)) return 0;
+  return std::max<int64_t>(avail / 8, (int64_t)256 << 20);
+}
+
 // One filtered incremental squaring T^_k = filter(2 T^_{k-1} + T^_{k-1}^2) (Eq. 4.15 with the
 // threshold of reading 8); deterministic, so a replay reproduces the forward exactly.  When
 // drop_input is given (the owner of T), it is released as soon as the product has been formed
 // (stream-ordered), so that T^_{k-1} is not held while the unfiltered T~_k is filtered.
+//
+// When T~_k does not fit in memory it is formed in chunks of consecutive rows.  Each chunk is
+// reduced at once to its entries above L = eps_g' / (2 sqrt(nnz(T~_k))), where eps_g' <= eps_g
+// is the bound from the rows formed so far (the norm ||I + T~_k||_F of reading 8 only grows as
+// rows are added); every threshold Algorithm 4.1 visits is >= eps_g / sqrt(nnz), so the entries
+// dropped here are dropped by every pass, and their sum of squares joins every pass's sum.  In
+// the symmetric mode a pair (i, j), (j, i) is decided once, by the row that forms its upper
+// entry; the lower entry takes that entry's value and decision.
 void square_step(const sexpm_options& o, const CsrD& T, int k, double a, double r0, bool sym, cudaStream_t s,
                  HostScalars& hs, RowStats& rs, CsrOwned& Tn, sexpm_step_stats* rec, const int32_t* sched,
                  CsrOwned* drop_input = nullptr) {
@@ -411,42 +478,148 @@ void square_step(const sexpm_options& o, const CsrD& T, int k, double a, double 
   const int64_t n = T.n;
   const int64_t nnz_in = T.nnz;
   const double ri = std::ldexp(r0, k);
-  CsrOwned Tt;
-  SpgemmTimes tm;
+  double ms_sym = 0.0, ms_num = 0.0;
+  ProductSym ps;
+  {
+    Timer t1(s);
+    product_symbolic(T, T, T, sym, nullptr, sched, &rs, s, hs, ps);
+    ms_sym = t1.ms();
+  }
+  const int64_t products = ps.products;
+  const int64_t in_bytes = 12 * nnz_in + 8 * (n + 1);
+  const int64_t limit = chunk_limit(o, ps.nnz, in_bytes, drop_input != nullptr);
   int64_t done = 0;
-  const int64_t prod = spgemm(T, T, T, 1.0, 2.0, s, Tt, &rs, hs, &tm, sym, &done, nullptr, sched);
-  if (drop_input) {
-    drop_input->rp.free();
-    drop_input->ci.free();
-    drop_input->v.free();
-  }
-  const double flops = 2.0 * (double)done + 2.0 * (double)nnz_in;
-  double normF = 1.0;
-  if (o.square_scale) {
-    const double sq = reduce_sum(rs.sq.p, n, s, hs);
-    const double tr = reduce_sum(rs.diag.p, n, s, hs);
-    const double f2 = sq + (double)n + 2.0 * tr;
+  int chunks = 1;
+  int64_t rows_class[kProductClasses] = {};
+  FilterOut fo;
+  double normF = 1.0, eps_g = 0.0;
+  int64_t nnz_raw = ps.nnz, nnz_stream = 0;
+  double bytes_stream = 0.0;
+  auto release_input = [&]() {
+    if (drop_input) {
+      drop_input->rp.free();
+      drop_input->ci.free();
+      drop_input->v.free();
+    }
+  };
+  auto eps_from_stats = [&](int64_t r1, double& sq_acc, double& tr_acc, int64_t from) {
+    // ||I + T~||_F^2 over the rows formed so far = sum sq + rows + 2 sum diag
+    if (!o.square_scale) return a * ri;
+    sq_acc += reduce_sum(rs.sq.p + from, r1 - from, s, hs);
+    tr_acc += reduce_sum(rs.diag.p + from, r1 - from, s, hs);
+    const double f2 = sq_acc + (double)r1 + 2.0 * tr_acc;
     normF = std::sqrt(f2 > 0.0 ? f2 : 0.0);
+    return a * ri * normF;
+  };
+  if (limit == 0) {
+    CsrOwned Tt;
+    Tt.n = n;
+    Tt.nnz = ps.nnz;
+    Tt.rp = std::move(ps.rp);
+    ps.rp_ext = Tt.rp.p;
+    Tt.ci.reset(Tt.nnz, s);
+    Tt.v.reset(Tt.nnz, s);
+    {
+      Timer t2(s);
+      done = product_numeric(ps, T, T, T, 1.0, 2.0, 0, n, 0, Tt.ci.p, Tt.v.p, &rs, s, hs);
+      if (sym) mirror_lower(Tt, s, hs);
+      ms_num = t2.ms();
+    }
+    release_input();
+    for (int c = 0; c < kProductClasses; ++c) rows_class[c] = ps.rows_numeric[c];
+    double sq = 0.0, tr = 0.0;
+    eps_g = eps_from_stats(n, sq, tr, 0);
+    fo = filter_alg41(Tt.view(), eps_g, o.e_r, o.max_filter_iters, s, Tn, hs);
+  } else {
+    // row boundaries from the product's row pointers
+    std::vector<int64_t> rph(n + 1);
+    SX_CUDA(cudaMemcpyAsync(rph.data(), ps.row_ptr(), (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SX_CUDA(cudaStreamSynchronize(s));
+    const int64_t per_chunk = std::max<int64_t>(1, limit / 12);
+    struct Owned {
+      DevBuf<int64_t> rp;
+      DevBuf<int32_t> ci;
+      DevBuf<double> v;
+    };
+    std::vector<Owned> owned;
+    std::vector<Piece> pieces;
+    DevBuf<Piece> dpieces;
+    double sq_acc = 0.0, tr_acc = 0.0, dropped = 0.0;
+    const double sqrt_nnz = std::sqrt((double)std::max<int64_t>(ps.nnz, 1));
+    chunks = 0;
+    double ms_drop = 0.0;
+    for (int64_t c0 = 0; c0 < n;) {
+      // the largest c1 with at most per_chunk entries in [c0, c1) (at least one row)
+      int64_t c1 = std::upper_bound(rph.begin() + c0 + 1, rph.end(), rph[c0] + per_chunk) - rph.begin() - 1;
+      if (c1 <= c0) c1 = c0 + 1;
+      const int64_t base = rph[c0], cn = rph[c1] - base;
+      DevBuf<int32_t> cci(cn, s);
+      DevBuf<double> cv(cn, s);
+      {
+        Timer t2(s);
+        done += product_numeric(ps, T, T, T, 1.0, 2.0, c0, c1, base, cci.p, cv.p, &rs, s, hs);
+        ms_num += t2.ms();
+      }
+      Timer t3(s);
+      const double eps_c = eps_from_stats(c1, sq_acc, tr_acc, c0);
+      const double L = 0.5 * eps_c / sqrt_nnz;
+      if (!pieces.empty()) {
+        dpieces.reset(pieces.size(), s);
+        SX_CUDA(cudaMemcpyAsync(dpieces.p, pieces.data(), pieces.size() * sizeof(Piece), cudaMemcpyHostToDevice, s));
+      }
+      DevBuf<int32_t> keep(c1 - c0, s);
+      dropped += drop_rows(c0, c1, ps.row_ptr(), base, cci.p, cv.p, sym, L, dpieces.p, (int)pieces.size(), keep.p, s,
+                           hs);
+      Owned ow;
+      ow.rp.reset(c1 - c0 + 1, s);
+      const int64_t kept = scan_counts(keep.p, c1 - c0, ow.rp.p, s, hs);
+      ow.ci.reset(kept, s);
+      ow.v.reset(kept, s);
+      compact_rows(c0, c1, ps.row_ptr(), base, cci.p, cv.p, sym, L, ow.rp.p, ow.ci.p, ow.v.p, s);
+      Piece pc;
+      pc.r0 = c0;
+      pc.r1 = c1;
+      pc.nnz = kept;
+      pc.rp = ow.rp.p;
+      pc.ci = ow.ci.p;
+      pc.v = ow.v.p;
+      pieces.push_back(pc);
+      owned.push_back(std::move(ow));
+      nnz_stream += kept;
+      bytes_stream += 24.0 * (double)cn + 12.0 * (double)kept + 24.0 * (double)(c1 - c0);
+      ms_drop += t3.ms();
+      ++chunks;
+      c0 = c1;
+    }
+    release_input();
+    for (int c = 0; c < kProductClasses; ++c) rows_class[c] = ps.rows_numeric[c];
+    ps = ProductSym();  // word patterns and row lists are no longer needed
+    dpieces.free();
+    eps_g = o.square_scale ? a * ri * normF : a * ri;  // normF now covers every row
+    fo = filter_alg41_pieces(pieces, n, dropped, eps_g, o.e_r, o.max_filter_iters, s, Tn, hs);
+    fo.ms += ms_drop;
+    fo.bytes += bytes_stream;
   }
-  const double eps_g = a * ri * normF;
-  FilterOut fo = filter_alg41(Tt.view(), eps_g, o.e_r, o.max_filter_iters, s, Tn, hs);
   if (rec) {
     std::memset(rec, 0, sizeof(*rec));
     rec->phase = 1;
     rec->i = k;
     rec->iters = fo.iters;
+    rec->chunks = chunks;
     rec->eps_g = eps_g;
     rec->t = fo.t;
     rec->b = fo.b;
     rec->norm_F = o.square_scale ? normF : 0.0;
-    rec->nnz_raw = Tt.nnz;
+    rec->nnz_raw = nnz_raw;
     rec->nnz = Tn.nnz;
-    rec->products = prod;
+    rec->nnz_stream = nnz_stream;
+    rec->products = products;
+    for (int c = 0; c < kProductClasses; ++c) rec->rows_class[c] = rows_class[c];
     rec->products_done = done;
-    rec->ms_symbolic = tm.ms_symbolic;
-    rec->ms_numeric = tm.ms_numeric;
+    rec->ms_symbolic = ms_sym;
+    rec->ms_numeric = ms_num;
     rec->ms_filter = fo.ms;
-    rec->flops = flops;
+    rec->flops = 2.0 * (double)done + 2.0 * (double)nnz_in;
     rec->bytes_filter = fo.bytes;
     rec->ms = ts.ms();
   }
@@ -616,6 +789,104 @@ CsrD with_values(const CsrD& P, const double* v) {
   return d;
 }
 
+// Reverse pass of the recorded forward run: dL/dH on the stored pattern of H into res->E for
+// dL/dE = W.  Returns the device milliseconds it took.
+double reverse_pass(sexpm_plan_t* p, const Record& rec, double tau, const sexpm_csr_view* W, sexpm_result* res) {
+  cudaStream_t s = p->s;
+  HostScalars& hs = p->hs;
+  const sexpm_options& o = p->opt;
+  Timer t_all(s);
+  CsrOwned Wd;
+  upload(*W, s, Wd, hs);
+  const CsrD Hp = p->H.view();
+  res->s = s;
+  std::memset(&res->st, 0, sizeof(res->st));
+  res->E.n = Hp.n;
+  res->E.nnz = Hp.nnz;
+  res->E.rp.reset(Hp.n + 1, s);
+  res->E.ci.reset(Hp.nnz, s);
+  res->E.v.reset(Hp.nnz, s);
+  SX_CUDA(cudaMemcpyAsync(res->E.rp.p, Hp.rp, (Hp.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  if (Hp.nnz) SX_CUDA(cudaMemcpyAsync(res->E.ci.p, Hp.ci, Hp.nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  CsrD none;
+  if (rec.M == 0) {
+    // ||tau H|| = 0: the method returns I; its first-order term is tau H, so dL/dH = tau W
+    sddmm(Hp, Wd.view(), none, 0.0, 1.0, false, res->E.v.p, s, hs);
+    scale_values(res->E.v.p, tau, Hp.nnz, res->E.v.p, s);
+  } else {
+    const int N = rec.N;
+    // dL/dT_N = W on the pattern of T^_N
+    CsrD TN = rec.T.at(N).view();
+    DevBuf<double> y(TN.nnz, s);
+    sddmm(TN, Wd.view(), none, 0.0, 1.0, false, y.p, s, hs);
+    CsrD Ypat = TN;                 // pattern of the current adjoint Y
+    CsrOwned Ykeep;                 // owns Y's pattern when it is not a checkpoint
+    std::map<int, CsrOwned> seg;    // replayed iterates of the current checkpoint segment
+    RowStats rs;
+    for (int k = N; k >= 1; --k) {
+      // T^_{k-1}: a checkpoint, or replayed from the checkpoint below it
+      const int km1 = k - 1;
+      if (!rec.T.count(km1) && !seg.count(km1)) {
+        seg.clear();
+        int c = km1;
+        while (!rec.T.count(c)) --c;
+        CsrD cur = rec.T.at(c).view();
+        for (int j = c + 1; j <= km1; ++j) {
+          square_step(o, cur, j, rec.a, rec.r0, false, s, hs, rs, seg[j], nullptr, p->sched.p);
+          cur = seg[j].view();
+        }
+      }
+      const CsrD Tp = rec.T.count(km1) ? rec.T.at(km1).view() : seg.at(km1).view();
+      // dL/dT_{k-1} = mask_{k-1}(2 Y + Y T^T + T^T Y)
+      const CsrD Y = with_values(Ypat, y.p);
+      CsrOwned Tpt, Yt;
+      transpose(Tp, s, Tpt, hs);
+      transpose(Y, s, Yt, hs);
+      DevBuf<double> g(Tp.nnz, s);
+      sddmm(Tp, Y, Tp, 1.0, 2.0, false, g.p, s, hs);
+      sddmm(Tp, Tpt.view(), Yt.view(), 1.0, 0.0, true, g.p, s, hs);
+      y = std::move(g);
+      // the new Y lives on the pattern of T^_{k-1}; keep that pattern alive
+      if (rec.T.count(km1)) {
+        Ypat = rec.T.at(km1).view();
+        Ykeep = CsrOwned();
+      } else {
+        CsrOwned pat;
+        copy_csr(Tp, s, pat);
+        Ykeep = std::move(pat);
+        Ypat = Ykeep.view();
+      }
+      if (rec.T.count(k) && k != N) { /* checkpoints stay until the end */ }
+      seg.erase(k);
+    }
+    // Taylor phase: dL/dS_i = dL/dT_0 on the pattern of S_i, then i = M'..2
+    const int Mp = (int)rec.S.size();
+    std::vector<DevBuf<double>> gs(Mp);
+    const CsrD GT0 = with_values(Ypat, y.p);
+    for (int i = 0; i < Mp; ++i) {
+      gs[i].reset(rec.S[i].nnz, s);
+      sddmm(rec.S[i].view(), GT0, none, 0.0, 1.0, false, gs[i].p, s, hs);
+    }
+    DevBuf<double> gh(Hp.nnz, s);
+    SX_CUDA(cudaMemsetAsync(gh.p, 0, Hp.nnz * sizeof(double), s));
+    const CsrD H0 = rec.H0.view();
+    for (int i = Mp; i >= 2; --i) {
+      const CsrD Yi = with_values(rec.S[i - 1].view(), gs[i - 1].p);
+      const CsrD Sp = rec.S[i - 2].view();
+      sddmm(Sp, Yi, H0, 1.0 / i, 0.0, true, gs[i - 2].p, s, hs);          // += mask(Y H_0^T)/i
+      CsrOwned Spt, Yit;
+      transpose(Sp, s, Spt, hs);
+      transpose(Yi, s, Yit, hs);
+      sddmm(Hp, Spt.view(), Yit.view(), 1.0 / i, 0.0, true, gh.p, s, hs);  // += mask_H(S^T Y)/i
+    }
+    sddmm(Hp, with_values(rec.S[0].view(), gs[0].p), none, 0.0, 1.0, true, gh.p, s, hs);  // += dL/dS_1
+    scale_values(gh.p, tau * std::ldexp(1.0, -N), Hp.nnz, res->E.v.p, s);
+  }
+  SX_CUDA(cudaStreamSynchronize(s));
+  res->st.nnz_out = res->E.nnz;
+  return t_all.ms();
+}
+
 #define SX_API_BEGIN try {
 #define SX_API_END                                         \
   }                                                        \
@@ -663,6 +934,7 @@ int sexpm_options_default(sexpm_options* opt) {
   opt->max_taylor = 1000;
   opt->symmetric = 1;
   opt->row_order = 1;
+  opt->chunk_bytes = 0;
   return SEXPM_OK;
 }
 
@@ -673,6 +945,7 @@ static void check_options(const sexpm_options& o) {
   if (o.max_filter_iters < 1 || o.n_extra < 0 || o.max_taylor < 1) fail(SEXPM_EINVAL, "bad iteration limits");
   if (o.symmetric != 0 && o.symmetric != 1) fail(SEXPM_EINVAL, "symmetric must be 0 or 1");
   if (o.row_order != 0 && o.row_order != 1) fail(SEXPM_EINVAL, "row_order must be 0 or 1");
+  if (o.chunk_bytes < 0) fail(SEXPM_EINVAL, "chunk_bytes must be >= 0");
 }
 
 int sexpm_plan(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_options* opt, void* stream,
@@ -777,10 +1050,20 @@ int sexpm_spgemm(const sexpm_csr_view* A, const sexpm_csr_view* B, const sexpm_c
   try {
     res->s = s;
     std::memset(&res->st, 0, sizeof(res->st));
-    const int64_t prod = spgemm(a.view(), b.view(), dv, div, beta, s, res->E, nullptr, hs);
+    sexpm_step_stats rec;
+    std::memset(&rec, 0, sizeof(rec));
+    int64_t done = 0;
+    const int64_t prod = spgemm(a.view(), b.view(), dv, div, beta, s, res->E, nullptr, hs, nullptr, false, &done,
+                                nullptr, nullptr, rec.rows_class);
     SX_CUDA(cudaStreamSynchronize(s));
     res->st.n = res->E.n;
     res->st.nnz_out = res->E.nnz;
+    rec.chunks = 1;
+    rec.nnz_raw = rec.nnz = res->E.nnz;
+    rec.products = prod;
+    rec.products_done = done;
+    res->steps.push_back(rec);
+    res->st.n_steps = 1;
     if (products) *products = prod;
   } catch (...) {
     delete res;
@@ -1113,125 +1396,80 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
   SX_API_END
 }
 
-int sexpm_adjoint(sexpm_plan_t* p, double tau, const sexpm_csr_view* W, int32_t ckpt_stride, sexpm_result_t** dH,
-                  sexpm_result_t** expm_out) {
+int sexpm_forward_keep(sexpm_plan_t* p, double tau, int32_t ckpt_stride, sexpm_result_t** expm_out,
+                       sexpm_tape_t** tape) {
   SX_API_BEGIN
-  if (!p || !W || !dH) fail(SEXPM_EINVAL, "null argument");
-  *dH = nullptr;
+  if (!p || !tape) fail(SEXPM_EINVAL, "null argument");
+  *tape = nullptr;
   if (expm_out) *expm_out = nullptr;
   if (p->count > 0) fail(SEXPM_EINVAL, "the adjoint takes a plain (non-batched) plan");
-  if (W->n != p->H.n) fail(SEXPM_EINVAL, "W must have the dimension of H");
   if (ckpt_stride < 0) fail(SEXPM_EINVAL, "ckpt_stride must be >= 0");
-  cudaStream_t s = p->s;
-  HostScalars& hs = p->hs;
-  const sexpm_options& o = p->opt;
-  Record rec;
-  rec.stride = ckpt_stride;
+  sexpm_tape_t* t = new sexpm_tape_t();
   sexpm_result* fwd = new sexpm_result();
+  try {
+    t->plan = p;
+    t->tau = tau;
+    t->rec.stride = ckpt_stride;
+    // forward with every product formed (the reverse pass differentiates exactly this map)
+    compute_impl(p, tau, fwd, &t->rec, false);
+    t->st = fwd->st;
+    t->steps = fwd->steps;
+  } catch (...) {
+    delete t;
+    delete fwd;
+    throw;
+  }
+  *tape = t;
+  if (expm_out) *expm_out = fwd; else delete fwd;
+  SX_API_END
+}
+
+int sexpm_adjoint_tape(sexpm_tape_t* t, const sexpm_csr_view* W, sexpm_result_t** dH) {
+  SX_API_BEGIN
+  if (!t || !W || !dH) fail(SEXPM_EINVAL, "null argument");
+  *dH = nullptr;
+  if (W->n != t->plan->H.n) fail(SEXPM_EINVAL, "W must have the dimension of H");
+  int dev = 0;
+  SX_CUDA(cudaGetDevice(&dev));
+  if (dev != t->plan->device) fail(SEXPM_EINVAL, "current device differs from the plan's device");
   sexpm_result* res = new sexpm_result();
   try {
-    // forward with every product formed (the reverse pass differentiates exactly this map)
-    compute_impl(p, tau, fwd, &rec, false);
-    Timer t_all(s);
-    CsrOwned Wd;
-    upload(*W, s, Wd, hs);
-    const CsrD Hp = p->H.view();
-    res->s = s;
-    std::memset(&res->st, 0, sizeof(res->st));
-    res->st = fwd->st;
-    res->steps = fwd->steps;
-    res->E.n = Hp.n;
-    res->E.nnz = Hp.nnz;
-    res->E.rp.reset(Hp.n + 1, s);
-    res->E.ci.reset(Hp.nnz, s);
-    res->E.v.reset(Hp.nnz, s);
-    SX_CUDA(cudaMemcpyAsync(res->E.rp.p, Hp.rp, (Hp.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    if (Hp.nnz) SX_CUDA(cudaMemcpyAsync(res->E.ci.p, Hp.ci, Hp.nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    CsrD none;
-    if (rec.M == 0) {
-      // ||tau H|| = 0: the method returns I; its first-order term is tau H, so dL/dH = tau W
-      sddmm(Hp, Wd.view(), none, 0.0, 1.0, false, res->E.v.p, s, hs);
-      scale_values(res->E.v.p, tau, Hp.nnz, res->E.v.p, s);
-    } else {
-      const int N = rec.N;
-      // dL/dT_N = W on the pattern of T^_N
-      CsrD TN = rec.T.at(N).view();
-      DevBuf<double> y(TN.nnz, s);
-      sddmm(TN, Wd.view(), none, 0.0, 1.0, false, y.p, s, hs);
-      CsrD Ypat = TN;                 // pattern of the current adjoint Y
-      CsrOwned Ykeep;                 // owns Y's pattern when it is not a checkpoint
-      std::map<int, CsrOwned> seg;    // replayed iterates of the current checkpoint segment
-      RowStats rs;
-      for (int k = N; k >= 1; --k) {
-        // T^_{k-1}: a checkpoint, or replayed from the checkpoint below it
-        const int km1 = k - 1;
-        if (!rec.T.count(km1) && !seg.count(km1)) {
-          seg.clear();
-          int c = km1;
-          while (!rec.T.count(c)) --c;
-          CsrD cur = rec.T.at(c).view();
-          for (int j = c + 1; j <= km1; ++j) {
-            square_step(o, cur, j, rec.a, rec.r0, false, s, hs, rs, seg[j], nullptr, p->sched.p);
-            cur = seg[j].view();
-          }
-        }
-        const CsrD Tp = rec.T.count(km1) ? rec.T.at(km1).view() : seg.at(km1).view();
-        // dL/dT_{k-1} = mask_{k-1}(2 Y + Y T^T + T^T Y)
-        const CsrD Y = with_values(Ypat, y.p);
-        CsrOwned Tpt, Yt;
-        transpose(Tp, s, Tpt, hs);
-        transpose(Y, s, Yt, hs);
-        DevBuf<double> g(Tp.nnz, s);
-        sddmm(Tp, Y, Tp, 1.0, 2.0, false, g.p, s, hs);
-        sddmm(Tp, Tpt.view(), Yt.view(), 1.0, 0.0, true, g.p, s, hs);
-        y = std::move(g);
-        // the new Y lives on the pattern of T^_{k-1}; keep that pattern alive
-        if (rec.T.count(km1)) {
-          Ypat = rec.T.at(km1).view();
-          Ykeep = CsrOwned();
-        } else {
-          CsrOwned pat;
-          copy_csr(Tp, s, pat);
-          Ykeep = std::move(pat);
-          Ypat = Ykeep.view();
-        }
-        if (rec.T.count(k) && k != N) { /* checkpoints stay until the end */ }
-        seg.erase(k);
-      }
-      // Taylor phase: dL/dS_i = dL/dT_0 on the pattern of S_i, then i = M'..2
-      const int Mp = (int)rec.S.size();
-      std::vector<DevBuf<double>> gs(Mp);
-      const CsrD GT0 = with_values(Ypat, y.p);
-      for (int i = 0; i < Mp; ++i) {
-        gs[i].reset(rec.S[i].nnz, s);
-        sddmm(rec.S[i].view(), GT0, none, 0.0, 1.0, false, gs[i].p, s, hs);
-      }
-      DevBuf<double> gh(Hp.nnz, s);
-      SX_CUDA(cudaMemsetAsync(gh.p, 0, Hp.nnz * sizeof(double), s));
-      const CsrD H0 = rec.H0.view();
-      for (int i = Mp; i >= 2; --i) {
-        const CsrD Yi = with_values(rec.S[i - 1].view(), gs[i - 1].p);
-        const CsrD Sp = rec.S[i - 2].view();
-        sddmm(Sp, Yi, H0, 1.0 / i, 0.0, true, gs[i - 2].p, s, hs);          // += mask(Y H_0^T)/i
-        CsrOwned Spt, Yit;
-        transpose(Sp, s, Spt, hs);
-        transpose(Yi, s, Yit, hs);
-        sddmm(Hp, Spt.view(), Yit.view(), 1.0 / i, 0.0, true, gh.p, s, hs);  // += mask_H(S^T Y)/i
-      }
-      sddmm(Hp, with_values(rec.S[0].view(), gs[0].p), none, 0.0, 1.0, true, gh.p, s, hs);  // += dL/dS_1
-      scale_values(gh.p, tau * std::ldexp(1.0, -N), Hp.nnz, res->E.v.p, s);
-    }
-    SX_CUDA(cudaStreamSynchronize(s));
-    res->st.ms_total = fwd->st.ms_total + t_all.ms();
+    res->st = t->st;
+    res->steps = t->steps;
+    res->st.ms_total = t->st.ms_total + reverse_pass(t->plan, t->rec, t->tau, W, res);
     res->st.nnz_out = res->E.nnz;
   } catch (...) {
-    delete fwd;
     delete res;
     throw;
   }
   *dH = res;
-  if (expm_out) *expm_out = fwd; else delete fwd;
   SX_API_END
+}
+
+void sexpm_tape_free(sexpm_tape_t* t) { delete t; }
+
+int sexpm_adjoint(sexpm_plan_t* p, double tau, const sexpm_csr_view* W, int32_t ckpt_stride, sexpm_result_t** dH,
+                  sexpm_result_t** expm_out) {
+  if (!p || !W || !dH) {
+    set_last_error("null argument");
+    return SEXPM_EINVAL;
+  }
+  *dH = nullptr;
+  if (expm_out) *expm_out = nullptr;
+  if (W->n != p->H.n) {
+    set_last_error("W must have the dimension of H");
+    return SEXPM_EINVAL;
+  }
+  sexpm_tape_t* tape = nullptr;
+  int rc = sexpm_forward_keep(p, tau, ckpt_stride, expm_out, &tape);
+  if (rc != SEXPM_OK) return rc;
+  rc = sexpm_adjoint_tape(tape, W, dH);
+  sexpm_tape_free(tape);
+  if (rc != SEXPM_OK && expm_out && *expm_out) {
+    sexpm_result_free(*expm_out);
+    *expm_out = nullptr;
+  }
+  return rc;
 }
 
 }  // extern "C"

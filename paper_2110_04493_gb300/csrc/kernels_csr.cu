@@ -1,8 +1,5 @@
 // Streaming CSR kernels of the method:
-//  * Algorithm 4.1 reduction passes (sum of squares of the stored entries with |v| <= t,
-//    fused with the per-row count of kept entries),
 //  * the scan allocator that turns per-row counts into int64 row pointers,
-//  * compaction of the kept entries (A~ = A - b_n of Algorithm 4.1),
 //  * the sparse sum T^_0 += S^_i (Algorithm 4.2 step 3) and e^H = I + T^_N (step 5),
 //  * norms, transposition, validation and equality tests used by the plan.
 // These are bound by HBM bandwidth; each reads its operands once with coalesced
@@ -85,32 +82,6 @@ __global__ void k_partial_sumsq(const double* x, int64_t n, double* part) {
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     s += x[i] * x[i];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-// Algorithm 4.1 pass, one warp per row: part[block] = sum over |v| <= t of v^2, keep[row] = #{|v| > t}.
-__global__ void k_filter_pass(CsrD A, double t, int32_t* keep, double* part) {
-  __shared__ double red[32];
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  double s = 0.0;
-  const unsigned long long tb = bits_of(t);
-  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
-    const int64_t q0 = A.rp[i], q1 = A.rp[i + 1];
-    int c = 0;
-    // four independent loads per lane and round (absent entries read as 0: dropped, adding 0)
-    for (int64_t q = q0 + lane_id(); q < q1; q += 128) {
-      double v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = q + 32 * u < q1 ? A.v[q + 32 * u] : 0.0;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (above(v[u], tb)) ++c; else s = fma(v[u], v[u], s);
-      }
-    }
-    c = warp_sum(c);
-    if (lane_id() == 0) keep[i] = c;
-  }
   s = block_sum(s, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
@@ -205,39 +176,6 @@ __global__ void k_scan_apply(const int32_t* cnt, int64_t n, const int64_t* tile_
     if (i < n) rp[i + 1] = run;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) rp[0] = 0;
-}
-
-// ---- compaction, warp per row: entries with |v| > t, order kept
-__global__ void k_compact(CsrD A, double t, const int64_t* rp_out, int32_t* ci_out, double* v_out) {
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const unsigned lt = (1u << lane_id()) - 1u;
-  const unsigned long long tb = bits_of(t);
-  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
-    const int64_t q0 = A.rp[i], q1 = A.rp[i + 1];
-    int64_t o = rp_out[i];
-    // four chunks of 32 per round: every load of the round is issued before the first store
-    for (int64_t qb = q0; qb < q1; qb += 128) {
-      double v[4];
-      int c[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t q = qb + 32 * u + lane_id();
-        v[u] = q < q1 ? A.v[q] : 0.0;
-        c[u] = q < q1 ? A.ci[q] : 0;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool keep = qb + 32 * u + lane_id() < q1 && above(v[u], tb);
-        const unsigned m = __ballot_sync(FULL, keep);
-        if (keep) {
-          const int64_t d = o + __popc(m & lt);
-          ci_out[d] = c[u];
-          v_out[d] = v[u];
-        }
-        o += __popc(m);
-      }
-    }
-  }
 }
 
 // ---- C = A + beta B, thread per row merge (rows of the Taylor terms are short)
@@ -584,15 +522,6 @@ double sum_squares(const CsrD& A, cudaStream_t s, HostScalars& hs) {
   return finish_partials(part.p, kRedBlocks, s, hs);
 }
 
-double filter_pass(const CsrD& A, double t, int32_t* keep, cudaStream_t s, HostScalars& hs) {
-  if (A.n == 0) return 0.0;
-  DevBuf<double> part(kRedBlocks, s);
-  k_filter_pass<<<kRedBlocks, kRedThreads, 0, s>>>(A, t, keep, part.p);
-  SX_CUDA(cudaGetLastError());
-  count_launches(1);
-  return finish_partials(part.p, kRedBlocks, s, hs);
-}
-
 int64_t scan_counts(const int32_t* cnt, int64_t n, int64_t* rp, cudaStream_t s, HostScalars& hs) {
   if (n == 0) {
     SX_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t), s));
@@ -608,14 +537,6 @@ int64_t scan_counts(const int32_t* cnt, int64_t n, int64_t* rp, cudaStream_t s, 
   SX_CUDA(cudaMemcpyAsync(hs.i, ts.p + tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   SX_CUDA(cudaStreamSynchronize(s));
   return hs.i[0];
-}
-
-void compact(const CsrD& A, double t, CsrOwned& C, cudaStream_t s) {
-  if (A.n == 0) return;
-  const int blocks = (int)std::min<int64_t>((A.n + 7) / 8, (int64_t)sm_count() * 64);
-  k_compact<<<blocks, 256, 0, s>>>(A, t, C.rp.p, C.ci.p, C.v.p);
-  SX_CUDA(cudaGetLastError());
-  count_launches(1);
 }
 
 void add(const CsrD& A, const CsrD& B, double beta, cudaStream_t s, CsrOwned& C, HostScalars& hs) {

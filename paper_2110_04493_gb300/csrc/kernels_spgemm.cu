@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstring>
 #include <cstdlib>
 #include <string>
 
@@ -40,7 +41,7 @@ namespace sexpm {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kClasses = 6;
+constexpr int kClasses = kProductClasses;
 // Shared-memory budget and block size of each row class; the last class uses global scratch.
 // Blocks have at most 256 threads; the numeric kernel is compiled for SEXPM_NUMERIC_BLOCKS
 // resident 256-thread blocks per SM (its register budget).
@@ -102,12 +103,7 @@ __host__ __device__ __forceinline__ long long numeric_need(long long W, long lon
   return need_bytes(W, cnt, cacc, ks_members(W, cnt, cacc, nwarps, sm_bytes));
 }
 
-// Word pattern of a CSR matrix: row r touches words wi[rp[r] .. rp[r+1]) with masks wb[...].
-struct WPat {
-  const int64_t* rp = nullptr;
-  const int32_t* wi = nullptr;
-  const uint32_t* wb = nullptr;
-};
+// (WPat, the word pattern of a CSR matrix, is declared in sexpm_internal.cuh.)
 
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
@@ -286,7 +282,7 @@ __global__ void k_analysis(CsrD A, CsrD B, CsrD D, const uint8_t* frozen, int32_
 // mode 0: symbolic need 4 W; mode 1: numeric need 12 W + 8 cnt.
 __global__ void k_classify(int64_t n, const int32_t* sched, const int32_t* words, const int64_t* rp_out,
                            const int32_t* cnt_up, int mode, int ks_bytes, int32_t* lists, int64_t list_stride,
-                           unsigned long long* counts, unsigned long long* maxneed) {
+                           unsigned long long* counts, unsigned long long* maxneed, int64_t r0, int64_t r1) {
   __shared__ unsigned int cnt[kClasses];
   __shared__ unsigned long long off[kClasses];
   if (threadIdx.x < kClasses) cnt[threadIdx.x] = 0;
@@ -296,7 +292,7 @@ __global__ void k_classify(int64_t n, const int32_t* sched, const int32_t* words
   int cls = -1;
   unsigned int slot = 0;
   long long need = 0;
-  if (t < n) {
+  if (t < n && i >= r0 && i < r1) {  // only the rows of [r0, r1) enter the lists
     const long long W = words[i];
     const long long full = mode == 0 ? 0 : rp_out[i + 1] - rp_out[i];
     const long long cacc = cnt_up ? (long long)cnt_up[i] : full;
@@ -771,7 +767,7 @@ __global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, C
                           int64_t nrows, const int32_t* base, const int32_t* words, const int64_t* rp_out,
                           int32_t* ci_out, double* v_out, double* row_sq, double* row_diag, unsigned char* gscratch,
                           int64_t gstride, unsigned long long* work_total, unsigned long long* row_ctr,
-                          int ks_bytes) {
+                          int ks_bytes, int64_t out_base) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned ured[32];
   __shared__ double dred[32];
@@ -786,8 +782,8 @@ __global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, C
     const int i = rows[r];
     const int W = words[i];
     const int b = base[i];
-    const int64_t o0 = rp_out[i];
-    const int cnt = (int)(rp_out[i + 1] - o0);
+    const int64_t o0 = rp_out[i] - out_base;  // row i's entries go to ci_out/v_out at rp_out[i] - out_base
+    const int cnt = (int)(rp_out[i + 1] - rp_out[i]);
     const int cacc = upper ? cnt_up[i] : cnt;   // entries accumulated: positions cnt - cacc .. cnt
     double* acc = reinterpret_cast<double*>(mem) - (cnt - cacc);  // indexed by full-row position
     unsigned* wk = reinterpret_cast<unsigned*>(mem);
@@ -949,59 +945,65 @@ void word_pattern(const CsrD& X, cudaStream_t s, WPatOwned& out, HostScalars& hs
 
 }  // namespace
 
-int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, cudaStream_t s, CsrOwned& C,
-               RowStats* stats, HostScalars& hs, SpgemmTimes* times, bool upper, int64_t* done,
-               const uint8_t* frozen, const int32_t* sched) {
+void product_symbolic(const CsrD& A, const CsrD& B, const CsrD& D, bool upper, const uint8_t* frozen,
+                      const int32_t* sched, RowStats* stats, cudaStream_t s, HostScalars& hs, ProductSym& ps) {
   const int64_t n = A.n;
-  EventPair ev_sym(times != nullptr, s), ev_num(times != nullptr, s);
   set_smem_limits();
-  C.n = n;
-  C.rp.reset(n + 1, s);
+  ps.n = n;
+  ps.upper = upper;
+  ps.frozen = frozen;
+  ps.sched = sched;
+  ps.hasD = D.n > 0;
+  ps.ks_bytes = ksplit_bytes();
+  ps.rp.reset(n + 1, s);
   if (stats) {
     stats->sq.reset(n, s);
     stats->diag.reset(n, s);
   }
   if (n == 0) {
-    SX_CUDA(cudaMemsetAsync(C.rp.p, 0, sizeof(int64_t), s));
-    C.nnz = 0;
-    return 0;
+    SX_CUDA(cudaMemsetAsync(ps.rp.p, 0, sizeof(int64_t), s));
+    ps.nnz = 0;
+    ps.products = 0;
+    return;
   }
-  const bool hasD = D.n > 0;
   const int sms = num_sms();
-  const int ks_bytes = ksplit_bytes();
-  ev_sym.start();
   WPatOwned wB, wD;
   word_pattern(B, s, wB, hs);
-  const bool same = hasD && D.rp == B.rp && D.ci == B.ci;
-  if (hasD && !same) word_pattern(D, s, wD, hs);
-  const WPat WB = wB.view();
-  const WPat WD = hasD ? (same ? WB : wD.view()) : WPat();
-  DevBuf<int32_t> base(n, s), words(n, s), cnt(n, s), lists((size_t)n * kClasses, s);
-  DevBuf<int32_t> cnt_up(upper ? n : 0, s);
+  ps.sameD = ps.hasD && D.rp == B.rp && D.ci == B.ci;
+  if (ps.hasD && !ps.sameD) word_pattern(D, s, wD, hs);
+  ps.wB_rp = std::move(wB.rp); ps.wB_wi = std::move(wB.wi); ps.wB_wb = std::move(wB.wb);
+  ps.wD_rp = std::move(wD.rp); ps.wD_wi = std::move(wD.wi); ps.wD_wb = std::move(wD.wb);
+  const WPat WB = ps.wpat_B(), WD = ps.wpat_D();
+  ps.base.reset(n, s);
+  ps.words.reset(n, s);
+  ps.cnt.reset(n, s);
+  ps.lists.reset((size_t)n * kClasses, s);
+  ps.cnt_up.reset(upper ? n : 0, s);
   DevBuf<int64_t> flops(n, s);
-  DevBuf<unsigned long long> ctr(2 * kClasses + 4, s);
-  SX_CUDA(cudaMemsetAsync(ctr.p, 0, ctr.count * sizeof(unsigned long long), s));
+  ps.ctr.reset(2 * kClasses + 4, s);
+  SX_CUDA(cudaMemsetAsync(ps.ctr.p, 0, ps.ctr.count * sizeof(unsigned long long), s));
   {
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((n + 7) / 8, (int64_t)sms * 64);
-    k_analysis<<<(unsigned)blocks, threads, 0, s>>>(A, B, D, frozen, base.p, words.p, flops.p);
+    k_analysis<<<(unsigned)blocks, threads, 0, s>>>(A, B, D, frozen, ps.base.p, ps.words.p, flops.p);
     SX_CUDA(cudaGetLastError());
-    k_sum_i64<<<(unsigned)std::min<int64_t>((n + 255) / 256, sms * 8), 256, 0, s>>>(flops.p, n, ctr.p + 2 * kClasses + 2);
-    k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, sched, words.p, nullptr, nullptr, 0, ks_bytes, lists.p,
-                                                         n, ctr.p, ctr.p + kClasses);
-    k_zero_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(words.p, n, stats ? stats->sq.p : nullptr,
-                                                         stats ? stats->diag.p : nullptr, cnt.p,
-                                                         upper ? cnt_up.p : nullptr);
+    k_sum_i64<<<(unsigned)std::min<int64_t>((n + 255) / 256, sms * 8), 256, 0, s>>>(flops.p, n,
+                                                                                 ps.ctr.p + 2 * kClasses + 2);
+    k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, sched, ps.words.p, nullptr, nullptr, 0, ps.ks_bytes,
+                                                         ps.lists.p, n, ps.ctr.p, ps.ctr.p + kClasses, 0, n);
+    k_zero_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ps.words.p, n, stats ? stats->sq.p : nullptr,
+                                                         stats ? stats->diag.p : nullptr, ps.cnt.p,
+                                                         upper ? ps.cnt_up.p : nullptr);
     SX_CUDA(cudaGetLastError());
     count_launches(4);
   }
-  // row counters of the dynamically scheduled symbolic and numeric launches, one per class each
-  DevBuf<unsigned long long> row_ctr(2 * kClasses, s);
-  SX_CUDA(cudaMemsetAsync(row_ctr.p, 0, row_ctr.count * sizeof(unsigned long long), s));
+  ps.row_ctr.reset(2 * kClasses, s);
+  SX_CUDA(cudaMemsetAsync(ps.row_ctr.p, 0, ps.row_ctr.count * sizeof(unsigned long long), s));
   unsigned long long h[2 * kClasses + 4];
-  SX_CUDA(cudaMemcpyAsync(h, ctr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SX_CUDA(cudaMemcpyAsync(h, ps.ctr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
   SX_CUDA(cudaStreamSynchronize(s));
-  const int64_t products = (int64_t)h[2 * kClasses + 2];
+  ps.products = (int64_t)h[2 * kClasses + 2];
+  for (int c = 0; c < kClasses; ++c) ps.rows_symbolic[c] = (int64_t)h[c];
   // symbolic pass per class
   {
     DevBuf<uint32_t> gs;
@@ -1013,82 +1015,118 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
       if (c < kClasses - 1) {
         const int bytes = (int)((need + 1023) & ~1023ll);
         const int64_t grid = std::min<int64_t>(nr, resident_blocks(k_symbolic<false>, threads, bytes));
-        k_symbolic<false><<<(unsigned)grid, threads, bytes, s>>>(A, WB, WD, hasD, frozen, lists.p + c * n, nr,
-                                                               base.p, words.p, cnt.p, upper ? cnt_up.p : nullptr,
-                                                               nullptr, 0, row_ctr.p + c);
+        k_symbolic<false><<<(unsigned)grid, threads, bytes, s>>>(A, WB, WD, ps.hasD, frozen, ps.lists.p + c * n, nr,
+                                                               ps.base.p, ps.words.p, ps.cnt.p,
+                                                               upper ? ps.cnt_up.p : nullptr, nullptr, 0,
+                                                               ps.row_ctr.p + c);
       } else {
         const int64_t stride = (need / 4 + 63) & ~63ll;
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
         gs.reset((size_t)(stride * grid), s);
-        k_symbolic<true><<<(unsigned)grid, threads, 0, s>>>(A, WB, WD, hasD, frozen, lists.p + c * n, nr, base.p,
-                                                          words.p, cnt.p, upper ? cnt_up.p : nullptr, gs.p, stride,
-                                                          row_ctr.p + c);
+        k_symbolic<true><<<(unsigned)grid, threads, 0, s>>>(A, WB, WD, ps.hasD, frozen, ps.lists.p + c * n, nr,
+                                                          ps.base.p, ps.words.p, ps.cnt.p,
+                                                          upper ? ps.cnt_up.p : nullptr, gs.p, stride,
+                                                          ps.row_ctr.p + c);
       }
       SX_CUDA(cudaGetLastError());
       count_launches(1);
     }
   }
-  // row pointers of C
-  SX_CUDA(cudaMemsetAsync(ctr.p, 0, ctr.count * sizeof(unsigned long long), s));
-  const int64_t total = scan_counts(cnt.p, n, C.rp.p, s, hs);
-  C.nnz = total;
-  C.ci.reset(total, s);
-  C.v.reset(total, s);
-  k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, sched, words.p, C.rp.p, upper ? cnt_up.p : nullptr, 1,
-                                                       ks_bytes, lists.p, n, ctr.p, ctr.p + kClasses);
+  // row pointers of the unfiltered product
+  ps.nnz = scan_counts(ps.cnt.p, n, ps.rp.p, s, hs);
+}
+
+int64_t product_numeric(ProductSym& ps, const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta,
+                        int64_t r0, int64_t r1, int64_t out_base, int32_t* ci_out, double* v_out, RowStats* stats,
+                        cudaStream_t s, HostScalars& hs) {
+  const int64_t n = ps.n;
+  if (n == 0 || r1 <= r0) return 0;
+  const int sms = num_sms();
+  const WPat WB = ps.wpat_B(), WD = ps.wpat_D();
+  const bool upper = ps.upper;
+  SX_CUDA(cudaMemsetAsync(ps.ctr.p, 0, ps.ctr.count * sizeof(unsigned long long), s));
+  SX_CUDA(cudaMemsetAsync(ps.row_ctr.p + kClasses, 0, kClasses * sizeof(unsigned long long), s));
+  k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, ps.sched, ps.words.p, ps.row_ptr(),
+                                                       upper ? ps.cnt_up.p : nullptr, 1, ps.ks_bytes, ps.lists.p, n,
+                                                       ps.ctr.p, ps.ctr.p + kClasses, r0, r1);
   SX_CUDA(cudaGetLastError());
   count_launches(1);
-  SX_CUDA(cudaMemcpyAsync(h, ctr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  unsigned long long h[2 * kClasses + 4];
+  SX_CUDA(cudaMemcpyAsync(h, ps.ctr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
   SX_CUDA(cudaStreamSynchronize(s));
-  if (times) times->ms_symbolic += ev_sym.stop();
-  ev_num.start();
-  {
-    DevBuf<unsigned char> gs;
-    for (int c = 0; c < kClasses; ++c) {
-      const int64_t nr = (int64_t)h[c];
-      if (!nr) continue;
-      const int threads = kClassThreads[c];
-      const int64_t need = (int64_t)h[kClasses + c];
-      if (c < kClasses - 1) {
-        const int bytes = (int)((need + 1023) & ~1023ll);
-        const int64_t grid = std::min<int64_t>(nr, resident_blocks(k_numeric<false>, threads, bytes));
-        k_numeric<false><<<(unsigned)grid, threads, bytes, s>>>(
-            A, B, D, WB, WD, div, beta, upper, frozen, upper ? cnt_up.p : nullptr, lists.p + c * n, nr, base.p, words.p, C.rp.p, C.ci.p, C.v.p,
-            stats ? stats->sq.p : nullptr, stats ? stats->diag.p : nullptr, nullptr, 0, ctr.p + 2 * kClasses + 3,
-            row_ctr.p + kClasses + c, ks_bytes);
-      } else {
-        const int64_t stride = (need + 255) & ~255ll;
-        const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
-        gs.reset((size_t)(stride * grid), s);
-        k_numeric<true><<<(unsigned)grid, threads, 0, s>>>(A, B, D, WB, WD, div, beta, upper, frozen,
-                                                         upper ? cnt_up.p : nullptr, lists.p + c * n,
-                                                         nr, base.p,
-                                                         words.p, C.rp.p, C.ci.p, C.v.p, stats ? stats->sq.p : nullptr,
-                                                         stats ? stats->diag.p : nullptr, gs.p, stride,
-                                                         ctr.p + 2 * kClasses + 3, row_ctr.p + kClasses + c, ks_bytes);
-      }
-      SX_CUDA(cudaGetLastError());
-      count_launches(1);
+  for (int c = 0; c < kClasses; ++c) ps.rows_numeric[c] += (int64_t)h[c];
+  DevBuf<unsigned char> gs;
+  for (int c = 0; c < kClasses; ++c) {
+    const int64_t nr = (int64_t)h[c];
+    if (!nr) continue;
+    const int threads = kClassThreads[c];
+    const int64_t need = (int64_t)h[kClasses + c];
+    if (c < kClasses - 1) {
+      const int bytes = (int)((need + 1023) & ~1023ll);
+      const int64_t grid = std::min<int64_t>(nr, resident_blocks(k_numeric<false>, threads, bytes));
+      k_numeric<false><<<(unsigned)grid, threads, bytes, s>>>(
+          A, B, D, WB, WD, div, beta, upper, ps.frozen, upper ? ps.cnt_up.p : nullptr, ps.lists.p + c * n, nr,
+          ps.base.p, ps.words.p, ps.row_ptr(), ci_out, v_out, stats ? stats->sq.p : nullptr,
+          stats ? stats->diag.p : nullptr, nullptr, 0, ps.ctr.p + 2 * kClasses + 3, ps.row_ctr.p + kClasses + c,
+          ps.ks_bytes, out_base);
+    } else {
+      const int64_t stride = (need + 255) & ~255ll;
+      const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
+      gs.reset((size_t)(stride * grid), s);
+      k_numeric<true><<<(unsigned)grid, threads, 0, s>>>(
+          A, B, D, WB, WD, div, beta, upper, ps.frozen, upper ? ps.cnt_up.p : nullptr, ps.lists.p + c * n, nr,
+          ps.base.p, ps.words.p, ps.row_ptr(), ci_out, v_out, stats ? stats->sq.p : nullptr,
+          stats ? stats->diag.p : nullptr, gs.p, stride, ps.ctr.p + 2 * kClasses + 3, ps.row_ctr.p + kClasses + c,
+          ps.ks_bytes, out_base);
     }
-  }
-  if (done) {
-    SX_CUDA(cudaMemcpyAsync(h + 2 * kClasses + 3, ctr.p + 2 * kClasses + 3, sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, s));
-    SX_CUDA(cudaStreamSynchronize(s));
-    *done = (int64_t)h[2 * kClasses + 3];
-  }
-  if (upper) {
-    SX_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long), s));
-    const int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)sms * 64);
-    k_mirror<<<blocks, 256, 0, s>>>(n, C.rp.p, C.ci.p, C.v.p, ctr.p);
     SX_CUDA(cudaGetLastError());
     count_launches(1);
-    SX_CUDA(cudaMemcpyAsync(h, ctr.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    SX_CUDA(cudaStreamSynchronize(s));
-    if (h[0] != 0) fail(SEXPM_ECUDA, "symmetric product: " + std::to_string(h[0]) + " entries without a mirror partner");
   }
+  SX_CUDA(cudaMemcpyAsync(h + 2 * kClasses + 3, ps.ctr.p + 2 * kClasses + 3, sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, s));
+  SX_CUDA(cudaStreamSynchronize(s));
+  return (int64_t)h[2 * kClasses + 3];
+}
+
+void mirror_lower(const CsrOwned& C, cudaStream_t s, HostScalars& hs) {
+  const int64_t n = C.n;
+  if (n == 0) return;
+  DevBuf<unsigned long long> miss(1, s);
+  SX_CUDA(cudaMemsetAsync(miss.p, 0, sizeof(unsigned long long), s));
+  const int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)num_sms() * 64);
+  k_mirror<<<blocks, 256, 0, s>>>(n, C.rp.p, C.ci.p, C.v.p, miss.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+  unsigned long long h = 0;
+  SX_CUDA(cudaMemcpyAsync(hs.i, miss.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  SX_CUDA(cudaStreamSynchronize(s));
+  std::memcpy(&h, hs.i, sizeof(h));
+  if (h != 0) fail(SEXPM_ECUDA, "symmetric product: " + std::to_string(h) + " entries without a mirror partner");
+}
+
+int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, cudaStream_t s, CsrOwned& C,
+               RowStats* stats, HostScalars& hs, SpgemmTimes* times, bool upper, int64_t* done,
+               const uint8_t* frozen, const int32_t* sched, int64_t* rows_class) {
+  const int64_t n = A.n;
+  EventPair ev_sym(times != nullptr, s), ev_num(times != nullptr, s);
+  ev_sym.start();
+  ProductSym ps;
+  product_symbolic(A, B, D, upper, frozen, sched, stats, s, hs, ps);
+  C.n = n;
+  C.nnz = ps.nnz;
+  C.rp = std::move(ps.rp);
+  ps.rp_ext = C.rp.p;  // the numeric pass reads the row pointers from C now
+  C.ci.reset(C.nnz, s);
+  C.v.reset(C.nnz, s);
+  if (times) times->ms_symbolic += ev_sym.stop();
+  ev_num.start();
+  const int64_t formed = product_numeric(ps, A, B, D, div, beta, 0, n, 0, C.ci.p, C.v.p, stats, s, hs);
+  if (done) *done = formed;
+  if (rows_class)
+    for (int c = 0; c < kClasses; ++c) rows_class[c] = ps.rows_numeric[c];
+  if (upper) mirror_lower(C, s, hs);
   if (times) times->ms_numeric += ev_num.stop();
-  return products;
+  return ps.products;
 }
 
 }  // namespace sexpm

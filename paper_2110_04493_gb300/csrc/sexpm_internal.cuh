@@ -127,8 +127,64 @@ struct SpgemmTimes {
   double ms_numeric = 0.0;   // the numeric pass (products, fused scaling and beta D)
 };
 
+// Word pattern of a CSR matrix: row r touches the 32-column words wi[rp[r] .. rp[r+1]) with the
+// column bits wb[...] inside each word.
+struct WPat {
+  const int64_t* rp = nullptr;
+  const int32_t* wi = nullptr;
+  const uint32_t* wb = nullptr;
+};
+
+// Symbolic phase of a sparse product C = (A B)/div + beta D, kept so that the numeric phase can
+// run on row ranges: word patterns of B (and D), per-row column span, per-row entry counts, the
+// row pointers of the unfiltered C, and the per-class row lists and counters.
+constexpr int kProductClasses = 6;
+struct ProductSym {
+  int64_t n = 0, products = 0, nnz = 0;
+  bool upper = false, hasD = false, sameD = false;
+  int ks_bytes = 0;
+  const uint8_t* frozen = nullptr;
+  const int32_t* sched = nullptr;
+  DevBuf<int64_t> wB_rp, wD_rp;
+  DevBuf<int32_t> wB_wi, wD_wi;
+  DevBuf<uint32_t> wB_wb, wD_wb;
+  DevBuf<int32_t> base, words, cnt, cnt_up, lists;
+  DevBuf<int64_t> rp;              // n + 1 row pointers of the unfiltered C
+  const int64_t* rp_ext = nullptr; // set when rp has been handed to an owner of C
+  DevBuf<unsigned long long> ctr, row_ctr;
+  int64_t rows_symbolic[kProductClasses] = {};  // rows per size class (symbolic pass)
+  int64_t rows_numeric[kProductClasses] = {};   // rows per size class, summed over numeric calls
+  const int64_t* row_ptr() const { return rp_ext ? rp_ext : rp.p; }
+  WPat wpat_B() const {
+    WPat w;
+    w.rp = wB_rp.p; w.wi = wB_wi.p; w.wb = wB_wb.p;
+    return w;
+  }
+  WPat wpat_D() const {
+    if (!hasD) return WPat();
+    if (sameD) return wpat_B();
+    WPat w;
+    w.rp = wD_rp.p; w.wi = wD_wi.p; w.wb = wD_wb.p;
+    return w;
+  }
+};
+
 // ---------------------------------------------------------------- kernels (launchers)
 // All launchers enqueue on stream s and do not synchronise unless stated.
+
+// Symbolic phase of C = (A B)/div + beta D (D.n == 0: absent): word patterns, row analysis,
+// size classes, per-row counts (and upper-part counts when upper) and the row pointers ps.rp;
+// allocates stats (n rows) when given and zeroes the statistics of empty rows.  Synchronises s.
+void product_symbolic(const CsrD& A, const CsrD& B, const CsrD& D, bool upper, const uint8_t* frozen,
+                      const int32_t* sched, RowStats* stats, cudaStream_t s, HostScalars& hs, ProductSym& ps);
+// Numeric phase for the rows [r0, r1): row i is written to ci_out/v_out at ps.row_ptr()[i] - out_base
+// (upper mode: the values below the diagonal are left for a mirror step).  Fills the statistics of
+// those rows.  Returns the products formed.  Synchronises s.
+int64_t product_numeric(ProductSym& ps, const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta,
+                        int64_t r0, int64_t r1, int64_t out_base, int32_t* ci_out, double* v_out, RowStats* stats,
+                        cudaStream_t s, HostScalars& hs);
+// Fills the values below the diagonal of a symmetric product from their mirror entries.
+void mirror_lower(const CsrOwned& C, cudaStream_t s, HostScalars& hs);
 
 // C = (A B) / div + beta D.  D may have n == 0 (absent).  Allocates C; fills row
 // statistics (sum of squares, diagonal) when stats != nullptr.  Synchronises s
@@ -140,25 +196,20 @@ struct SpgemmTimes {
 // copy of D_i (used by the batched method for instances that have finished their squarings).
 // sched (optional, n row ids): the order in which rows are handed to the thread blocks (a
 // permutation chosen for cache locality; results do not depend on it).
+// rows_class (optional, kProductClasses entries) receives the rows of the numeric pass per size class.
 int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, cudaStream_t s,
                CsrOwned& C, RowStats* stats, HostScalars& hs, SpgemmTimes* times = nullptr, bool upper = false,
-               int64_t* done = nullptr, const uint8_t* frozen = nullptr, const int32_t* sched = nullptr);
+               int64_t* done = nullptr, const uint8_t* frozen = nullptr, const int32_t* sched = nullptr,
+               int64_t* rows_class = nullptr);
 
 // sum_i x[i] over n doubles, deterministic order.  Synchronises and returns the sum.
 double reduce_sum(const double* x, int64_t n, cudaStream_t s, HostScalars& hs);
 // sum over the stored values of A of v^2.
 double sum_squares(const CsrD& A, cudaStream_t s, HostScalars& hs);
 
-// One Algorithm 4.1 pass: returns sum_{|v| <= t} v^2 over the stored values of A and
-// writes keep[i] = #{ |v| > t } for every row.  Synchronises s.
-double filter_pass(const CsrD& A, double t, int32_t* keep, cudaStream_t s, HostScalars& hs);
-
 // Exclusive scan of int32 counts into int64 row pointers (n+1 entries).  Returns the total
 // (synchronises s).
 int64_t scan_counts(const int32_t* cnt, int64_t n, int64_t* rp, cudaStream_t s, HostScalars& hs);
-
-// Copy the entries of A with |v| > t into C (rows given by C.rp, already scanned).
-void compact(const CsrD& A, double t, CsrOwned& C, cudaStream_t s);
 
 // C = A + beta B (union pattern).
 void add(const CsrD& A, const CsrD& B, double beta, cudaStream_t s, CsrOwned& C, HostScalars& hs);
@@ -180,6 +231,37 @@ bool csr_equal(const CsrD& A, const CsrD& B, double sign, cudaStream_t s, HostSc
 
 // Validation on device: sorted unique in-range columns, finite values, monotone row_ptr.
 bool csr_valid(const CsrD& A, cudaStream_t s, HostScalars& hs);
+
+// ---------------------------------------------------------------- Algorithm 4.1 over row pieces
+// A block of rows [r0, r1) of a sparse matrix with local row pointers (rp[0] = 0, r1 - r0 + 1
+// entries, rp[r1 - r0] = nnz).  A whole matrix is one piece (r0 = 0, r1 = n).
+struct Piece {
+  int64_t r0 = 0, r1 = 0, nnz = 0;
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const double* v = nullptr;
+};
+
+// Tiles of the flat filter kernels covering nnz entries.
+int64_t tiles_of(int64_t nnz);
+// One Algorithm 4.1 pass over all pieces: returns sum_{|v| <= t} v^2 and writes the kept
+// count (|v| > t) of every tile (piece p's tiles start at tile_cnt + tile_base[p]).
+// Synchronises s.
+double pass_pieces(const std::vector<Piece>& P, const std::vector<int64_t>& tile_base, double t, int32_t* tile_cnt,
+                   cudaStream_t s, HostScalars& hs);
+// Compaction of the entries |v| > t of all pieces into out (rows 0..n-1; out.rp/ci/v allocated);
+// tile_off = exclusive scan of the tile counts of the last pass (total at tile_off[total tiles]).
+void compact_pieces(const std::vector<Piece>& P, const std::vector<int64_t>& tile_base, double t,
+                    const int64_t* tile_off, int64_t n, CsrOwned& out, cudaStream_t s);
+// Exact streaming step of a row chunk [r0, r1) of an unfiltered product (row i at
+// rp[i] - base of ci/v): per-row kept counts at the lower bound L (keep, r1 - r0 entries) and the
+// returned sum of squares of the dropped entries; in the symmetric mode lower entries take their
+// mirror's value and decision (same chunk, or the earlier device pieces).  Synchronises s.
+double drop_rows(int64_t r0, int64_t r1, const int64_t* rp, int64_t base, const int32_t* ci, double* v, bool sym,
+                 double L, const Piece* pieces, int npieces, int32_t* keep, cudaStream_t s, HostScalars& hs);
+// Copies the entries drop_rows kept into a piece (out_rp: scanned keep, r1 - r0 + 1 entries).
+void compact_rows(int64_t r0, int64_t r1, const int64_t* rp, int64_t base, const int32_t* ci, const double* v, bool sym,
+                  double L, const int64_t* out_rp, int32_t* out_ci, double* out_v, cudaStream_t s);
 
 // ---------------------------------------------------------------- batched (block-diagonal) helpers
 // inst[i]: instance of row i; seg[b] .. seg[b+1]: rows of instance b (device arrays).

@@ -38,16 +38,16 @@ class CsrView(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("e_r", ctypes.c_double), ("square_scale", ctypes.c_int32), ("normal_override", ctypes.c_int32),
                 ("max_filter_iters", ctypes.c_int32), ("n_extra", ctypes.c_int32), ("max_taylor", ctypes.c_int32),
-                ("symmetric", ctypes.c_int32), ("row_order", ctypes.c_int32)]
+                ("symmetric", ctypes.c_int32), ("row_order", ctypes.c_int32), ("chunk_bytes", ctypes.c_int64)]
 
 
 class StepStats(ctypes.Structure):
-    _fields_ = [("phase", ctypes.c_int32), ("i", ctypes.c_int32), ("iters", ctypes.c_int32), ("pad_", ctypes.c_int32),
+    _fields_ = [("phase", ctypes.c_int32), ("i", ctypes.c_int32), ("iters", ctypes.c_int32), ("chunks", ctypes.c_int32),
                 ("eps_g", ctypes.c_double), ("t", ctypes.c_double), ("b", ctypes.c_double),
                 ("norm_F", ctypes.c_double), ("nnz_raw", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("products", ctypes.c_int64), ("products_done", ctypes.c_int64), ("ms", ctypes.c_double), ("ms_symbolic", ctypes.c_double),
                 ("ms_numeric", ctypes.c_double), ("ms_filter", ctypes.c_double), ("flops", ctypes.c_double),
-                ("bytes_filter", ctypes.c_double)]
+                ("bytes_filter", ctypes.c_double), ("nnz_stream", ctypes.c_int64), ("rows_class", ctypes.c_int64 * 6)]
 
 
 class Stats(ctypes.Structure):
@@ -98,6 +98,10 @@ def load() -> ctypes.CDLL:
     L.sexpm_plan_batched.argtypes = [P(CsrView), ctypes.c_int32, ctypes.c_double, P(Options), vp, P(vp)]
     L.sexpm_compute_batched.argtypes = [vp, P(ctypes.c_double), P(vp)]
     L.sexpm_adjoint.argtypes = [vp, ctypes.c_double, P(CsrView), ctypes.c_int32, P(vp), P(vp)]
+    L.sexpm_forward_keep.argtypes = [vp, ctypes.c_double, ctypes.c_int32, P(vp), P(vp)]
+    L.sexpm_adjoint_tape.argtypes = [vp, P(CsrView), P(vp)]
+    L.sexpm_tape_free.argtypes = [vp]
+    L.sexpm_tape_free.restype = None
     L.sexpm_filter_noalloc.argtypes = [P(CsrView), ctypes.c_double, ctypes.c_double, ctypes.c_int32, vp, vp, vp, vp,
                                        ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_int32),
                                        P(ctypes.c_double)]
@@ -220,8 +224,8 @@ class Result:
         steps = (StepStats * 512)()
         _check(load().sexpm_stats(self._h, ctypes.byref(st), steps, 512))
         d = {f: getattr(st, f) for f, _ in Stats._fields_}
-        d["steps"] = [{f: getattr(steps[k], f) for f, _ in StepStats._fields_ if f != "pad_"}
-                      for k in range(min(st.n_steps, 512))]
+        d["steps"] = [{f: (list(getattr(steps[k], f)) if f == "rows_class" else getattr(steps[k], f))
+                       for f, _ in StepStats._fields_} for k in range(min(st.n_steps, 512))]
         return d
 
     def free(self) -> None:
@@ -255,6 +259,13 @@ class Plan:
         _check(load().sexpm_compute(self._h, float(tau), ctypes.byref(r)))
         return Result(r.value)
 
+    def forward_keep(self, tau: float = 1.0, ckpt_stride: int = 0) -> Tuple["Tape", Result]:
+        """sexpm_forward_keep: e^{tau H} (every product formed) and a Tape holding the checkpoints
+        its reverse pass needs."""
+        t, r = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(load().sexpm_forward_keep(self._h, float(tau), int(ckpt_stride), ctypes.byref(r), ctypes.byref(t)))
+        return Tape(t.value, self), Result(r.value)
+
     def close(self) -> None:
         if self._h:
             load().sexpm_plan_destroy(self._h)
@@ -267,6 +278,38 @@ class Plan:
             pass
 
 
+class Tape:
+    """A kept forward run (sexpm_forward_keep); adjoint(W) runs the reverse pass (sexpm_adjoint_tape).
+    Holds a reference to its plan, which must stay open while the tape is alive."""
+
+    def __init__(self, handle: int, plan: Plan):
+        self._h = ctypes.c_void_p(handle)
+        self.plan = plan
+
+    def adjoint(self, W, device="cuda"):
+        """dL/dH on the stored pattern of H for dL/dE = W: (row_ptr, col, val) torch tensors."""
+        keep: List[Any] = []
+        w = _make_view(W, keep)
+        r = ctypes.c_void_p()
+        _check(load().sexpm_adjoint_tape(self._h, ctypes.byref(w), ctypes.byref(r)))
+        res = Result(r.value)
+        try:
+            return res.to_torch(device)
+        finally:
+            res.free()
+
+    def free(self) -> None:
+        if self._h:
+            load().sexpm_tape_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 def expm(H, tau: float = 1.0, eps: float = 1e-12, device="cuda", **opts):
     """e^{tau H} as (row_ptr, col, val) torch tensors on `device`, plus the stats dict.  When H is
     a torch.sparse_csr tensor, e^{tau H} is returned as one too (float64, int64 indices)."""
@@ -274,6 +317,7 @@ def expm(H, tau: float = 1.0, eps: float = 1e-12, device="cuda", **opts):
     try:
         res = plan.compute(tau)
         try:
+            release_memory()  # the pool's cached working memory goes back before the copy is allocated
             out = res.to_torch(device)
             st = res.stats()
         finally:
@@ -379,6 +423,23 @@ def spgemm(A, B, D=None, div: float = 1.0, beta: float = 0.0, device="cuda"):
         res.free()
 
 
+def spgemm_rows_per_class(A, B, D=None, div: float = 1.0, beta: float = 0.0) -> List[int]:
+    """Rows of the numeric pass of sexpm_spgemm per size class (shared memory 8, 24, 56, 112 and
+    220 KB, then global memory), from the step record of its result."""
+    keep: List[Any] = []
+    a, b = _make_view(A, keep), _make_view(B, keep)
+    d = _make_view(D, keep) if D is not None else None
+    r = ctypes.c_void_p()
+    prod = ctypes.c_int64()
+    _check(load().sexpm_spgemm(ctypes.byref(a), ctypes.byref(b), ctypes.byref(d) if d is not None else None,
+                               float(div), float(beta), _stream_ptr(), ctypes.byref(r), ctypes.byref(prod)))
+    res = Result(r.value)
+    try:
+        return list(res.stats()["steps"][0]["rows_class"])
+    finally:
+        res.free()
+
+
 def filter_csr(A, eps_g: float, e_r: float = 0.1, max_iters: int = 100, device="cuda"):
     """Algorithm 4.1 through sexpm_filter; returns ((row_ptr, col, val), t, iters, b)."""
     keep: List[Any] = []
@@ -452,26 +513,39 @@ def _autograd_class():
     import torch
 
     class SexpmFn(torch.autograd.Function):
-        """e^{tau H} with a gradient: forward(h_val, row_ptr, col, n, tau, eps) returns the
-        values of E = e^{tau H} and its pattern (row_ptr, col, non-differentiable); backward
-        maps dL/d(E values) to dL/d(h_val) through sexpm_adjoint (masks frozen)."""
+        """e^{tau H} with a gradient, for H = beta A where A has the values `values_of_A` on a fixed
+        sparse pattern = (row_ptr, col, n).  forward returns the values of E = e^{tau H} and its
+        pattern (row_ptr, col; not differentiable); it keeps the forward's checkpoints
+        (sexpm_forward_keep), and backward maps dL/d(E values) to dL/dA = beta dL/dH through
+        sexpm_adjoint_tape (the filter decisions of the forward held fixed)."""
 
         @staticmethod
-        def forward(ctx, h_val, row_ptr, col, n, tau, eps, ckpt_stride=0):
-            H = (row_ptr, col, h_val.detach(), int(n))
-            (erp, eci, ev), st = expm(H, tau, eps, device=h_val.device, symmetric=0)
-            ctx.save_for_backward(h_val.detach(), row_ptr, col, erp, eci)
-            ctx.n, ctx.tau, ctx.eps, ctx.stride = int(n), float(tau), float(eps), int(ckpt_stride)
+        def forward(ctx, values_of_A, pattern, beta, tau, eps, ckpt_stride=0):
+            row_ptr, col, n = pattern
+            H = (row_ptr, col, float(beta) * values_of_A.detach(), int(n))
+            plan = Plan(H, eps, symmetric=0)
+            tape, res = plan.forward_keep(tau, ckpt_stride)
+            try:
+                erp, eci, ev = res.to_torch(values_of_A.device)
+            finally:
+                res.free()
+            ctx.tape, ctx.beta, ctx.n = tape, float(beta), int(n)
+            ctx.save_for_backward(erp, eci)
             ctx.mark_non_differentiable(erp, eci)
             return ev, erp, eci
 
         @staticmethod
         def backward(ctx, g_ev, g_erp=None, g_eci=None):
-            h_val, row_ptr, col, erp, eci = ctx.saved_tensors
-            W = (erp, eci, g_ev.contiguous(), ctx.n)
-            _, _, g = adjoint((row_ptr, col, h_val, ctx.n), ctx.tau, ctx.eps, W, ckpt_stride=ctx.stride,
-                              device=h_val.device, symmetric=0)
-            return g, None, None, None, None, None, None
+            erp, eci = ctx.saved_tensors
+            tape = ctx.tape
+            try:
+                _, _, g = tape.adjoint((erp, eci, g_ev.contiguous(), ctx.n), device=g_ev.device)
+            finally:
+                plan = tape.plan
+                tape.free()
+                plan.close()
+                ctx.tape = None
+            return ctx.beta * g, None, None, None, None, None
 
     return SexpmFn
 
@@ -479,9 +553,44 @@ def _autograd_class():
 _sexpm_fn = None
 
 
-def expm_autograd(h_val, row_ptr, col, n, tau, eps, ckpt_stride=0):
-    """Differentiable e^{tau H}: returns (E values, E row_ptr, E col); gradients flow to h_val."""
+def sexpm_fn():
+    """The torch.autograd.Function SexpmFn: SexpmFn.apply(values_of_A, (row_ptr, col, n), beta, tau, eps
+    [, ckpt_stride]) -> (E values, E row_ptr, E col)."""
     global _sexpm_fn
     if _sexpm_fn is None:
         _sexpm_fn = _autograd_class()
-    return _sexpm_fn.apply(h_val, row_ptr, col, n, tau, eps, ckpt_stride)
+    return _sexpm_fn
+
+
+def expm_autograd(h_val, row_ptr, col, n, tau, eps, ckpt_stride=0):
+    """Differentiable e^{tau H} for H given by its values h_val on (row_ptr, col): returns
+    (E values, E row_ptr, E col); gradients flow to h_val."""
+    return sexpm_fn().apply(h_val, (row_ptr, col, int(n)), 1.0, tau, eps, ckpt_stride)
+
+
+def edge_pattern(edge_index, n: int):
+    """Symmetric CSR pattern of an undirected graph given by its edges (2 x m, u != v, each edge
+    once): returns (row_ptr int64, col int32, entry_edge int64), entry_edge[p] the edge of stored
+    entry p (both (u, v) and (v, u) map to the same edge)."""
+    ei = np.asarray(edge_index, dtype=np.int64)
+    m = ei.shape[1]
+    rows = np.concatenate([ei[0], ei[1]])
+    cols = np.concatenate([ei[1], ei[0]])
+    eid = np.concatenate([np.arange(m), np.arange(m)])
+    order = np.lexsort((cols, rows))
+    rows, cols, eid = rows[order], cols[order], eid[order]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    return np.cumsum(row_ptr), cols.astype(np.int32), eid
+
+
+def expm_edges(w, edge_index, n: int, beta: float, tau: float, eps: float, ckpt_stride: int = 0):
+    """e^{tau beta A} for the symmetric weighted adjacency A of an undirected graph with edge
+    weights w (torch tensor, one per edge of edge_index, 2 x m): returns (E values, E row_ptr,
+    E col); dL/dw_e = beta (dL/dH_uv + dL/dH_vu) flows back to w."""
+    import torch
+    rp, ci, eid = edge_pattern(edge_index, n)
+    dev = w.device
+    vals = w[torch.from_numpy(eid).to(dev)]
+    return sexpm_fn().apply(vals, (torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), int(n)), beta, tau, eps,
+                            ckpt_stride)

@@ -40,7 +40,31 @@ def expm_parity(G: sp.csr_matrix, R: sp.csr_matrix, t_drop: float, rtol: float =
     vr = np.abs(np.asarray(R[only_r.row, only_r.col]).ravel()) if only_r.nnz else np.zeros(0)
     worst_flip = float(max(vg.max() if vg.size else 0.0, vr.max() if vr.size else 0.0))
     out = {"maxabs": maxabs, "norm1": n1, "only_gpu": int(only_g.nnz), "only_oracle": int(only_r.nnz),
-           "worst_flip": worst_flip, "nnz_gpu": int(G.nnz), "nnz_oracle": int(R.nnz)}
+           "worst_flip": worst_flip, "nnz_gpu": int(G.nnz), "nnz_oracle": int(R.nnz), "t_drop": t_drop}
+    DROP_FLIPS.append(out)
     assert maxabs <= rtol * max(n1, 1e-300), out
     assert worst_flip <= 2.0 * t_drop, out
     return out
+
+
+# Every expm_parity call of the session, for the drop-decision summary printed at the end of the
+# run (entries stored by one side only, i.e. filter decisions that differ, and their size against
+# the drop threshold).
+DROP_FLIPS: list = []
+
+
+def taylor_time_stepper(Ht, R, substeps: int, rel_stop: float = 1e-20):
+    """e^H R by `substeps` steps of a truncated Taylor series of e^{H/substeps} applied to the block
+    of vectors R (torch sparse CSR H on the GPU, cuSPARSE products): each step sums terms until one
+    falls below rel_stop of the running sum.  Independent of the library's method."""
+    import torch
+    Y = R.clone()
+    for _ in range(substeps):
+        term, acc = Y.clone(), Y.clone()
+        for k in range(1, 80):
+            term = torch.sparse.mm(Ht, term) / (substeps * k)
+            acc = acc + term
+            if term.abs().max() <= rel_stop * acc.abs().max():
+                break
+        Y = acc
+    return Y

@@ -99,3 +99,49 @@ def test_autograd_function(sx):
     Go, E, st, tr = O.adjoint(H.to_scipy(), tau, 1e-12, W.to_scipy())
     ref = np.asarray(Go[np.repeat(np.arange(H.n), np.diff(H.row_ptr)), np.array(H.col, dtype=np.int64)]).ravel()
     assert np.abs(hv.grad.cpu().numpy() - ref).max() <= 1e-9 * max(np.abs(ref).max(), 1e-300)
+
+
+def test_forward_keep_tape_matches_adjoint(sx):
+    """sexpm_forward_keep + sexpm_adjoint_tape return exactly what sexpm_adjoint returns (same
+    forward, same checkpoints), and one kept forward serves two loss weights."""
+    H, tau = _cases()["graph"]
+    W1, W2 = _W(H.n, 21), _W(H.n, 22)
+    plan = sx.Plan(torch_csr(H), 1e-12)
+    try:
+        tape, res = plan.forward_keep(tau)
+        res.free()
+        g1 = tape.adjoint(torch_csr(W1))
+        g2 = tape.adjoint(torch_csr(W2))
+        tape.free()
+        r1 = sx.adjoint(plan, tau, 1e-12, torch_csr(W1))
+        r2 = sx.adjoint(plan, tau, 1e-12, torch_csr(W2))
+    finally:
+        plan.close()
+    for g, r in ((g1, r1), (g2, r2)):
+        assert np.array_equal(g[0].cpu().numpy(), r[0].cpu().numpy())
+        assert np.array_equal(g[2].cpu().numpy(), r[2].cpu().numpy())
+
+
+def test_autograd_edge_parameterisation(sx):
+    """SexpmFn in the edge form: H = beta A for the symmetric weighted adjacency A of a graph
+    given by its edge list and one weight per edge; dL/dw_e = beta (dL/dH_uv + dL/dH_vu) against
+    the oracle's adjoint."""
+    import torch
+    A = rgg_adjacency(500, seed=9)
+    beta, tau = 0.5, 1.0
+    Au = sp.triu(A.to_scipy(), 1).tocoo()
+    edges = np.vstack([Au.row, Au.col])
+    w = torch.from_numpy(Au.data.copy()).cuda().requires_grad_(True)
+    ev, erp, eci = sx.expm_edges(w, edges, A.n, beta, tau, 1e-12)
+    W = _W(A.n, 23)
+    Wd = W.to_scipy().tocsr()
+    erp_h = np.array(erp.cpu().numpy(), dtype=np.int64, copy=True)
+    eci_h = np.array(eci.cpu().numpy(), dtype=np.int64, copy=True)
+    rows = np.repeat(np.arange(A.n), np.diff(erp_h))
+    w_on_E = torch.from_numpy(np.asarray(Wd[rows, eci_h]).ravel().copy()).cuda()
+    (ev * w_on_E).sum().backward()
+    Go, E, st, tr = O.adjoint(beta * A.to_scipy(), tau, 1e-12, W.to_scipy())
+    Go = sp.csr_matrix(Go)
+    ref = beta * (np.asarray(Go[Au.row, Au.col]).ravel() + np.asarray(Go[Au.col, Au.row]).ravel())
+    got = w.grad.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-9 * max(np.abs(ref).max(), 1e-300)

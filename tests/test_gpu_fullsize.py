@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from tests._compare import torch_csr
+from tests._compare import taylor_time_stepper, torch_csr
 from workloads import dirichlet_laplacian, get_config, rgg_adjacency, sparse_loss_weights
 
 pytestmark = pytest.mark.gpu
@@ -58,23 +58,68 @@ def test_lap2d_m1500_rows_match_kronecker_closed_form(sx):
     assert (st["M"], st["N"]) == (18, 14)
 
 
-def test_lap3d_rows_match_kronecker_closed_form(sx):
-    """The 3-D workload's tau/h^2 = 2.1125 and eps = 1e-12 on a 32^3 grid (the 64^3 grid's
-    unfiltered products exceed one GPU's memory in this build): sampled rows against
-    e^{tau L_1} (x) e^{tau L_1} (x) e^{tau L_1}."""
-    m = 32
-    tau = 2.1125 / (m + 1) ** 2
-    H = dirichlet_laplacian(m, 3)
-    (rp, ci, v), st = sx.expm(torch_csr(H), tau, 1e-12)
-    E1 = _sine_basis_expm(m, tau)
+def _free_cached():
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def test_lap3d_m64_rows_match_kronecker_closed_form(sx):
+    """The 3-D workload at full size (64^3 grid, n = 262,144, tau = 5e-4, eps = 1e-12): its
+    last unfiltered products do not fit in memory whole, so they are formed in row chunks with
+    Algorithm 4.1 streamed exactly.  Sampled full rows against
+    e^{tau L_1} (x) e^{tau L_1} (x) e^{tau L_1}, max-abs <= 1e-12 ||e^H||_1 (<= 1e-12)."""
+    _free_cached()
+    c = get_config("lap3d_m64")
+    H = c.build()
+    (rp, ci, v), st = sx.expm(torch_csr(H), c.tau, c.eps)
+    m = 64
+    E1 = _sine_basis_expm(m, c.tau)
     rng = np.random.default_rng(6)
-    rows = list(rng.integers(0, H.n, size=24)) + [0, H.n - 1, H.n // 2]
+    rows = list(rng.integers(0, H.n, size=40)) + [0, m - 1, H.n - 1, H.n // 2, 32 + 64 * 32 + 4096 * 32,
+                                                   5 + 64 * 63 + 4096 * 10]
     for i, (cols, vals) in zip(rows, _rows(rp, ci, v, rows)):
         x, y, z = i % m, (i // m) % m, i // (m * m)
         exact = np.einsum("a,b,c->abc", E1[z], E1[y], E1[x]).ravel()
         got = np.zeros(H.n)
         got[cols] = vals
         assert np.abs(got - exact).max() <= 1e-12, i
+    sq = [r for r in st["steps"] if r["phase"] == 1]
+    print(f"lap3d_m64: M={st['M']} N={st['N']} nnz(e^H)={st['nnz_out']} peak={st['peak_bytes'] / 2**30:.1f} GiB "
+          f"chunks={[r['chunks'] for r in sq]} ms={st['ms_total']:.0f}")
+    del rp, ci, v
+    _free_cached()
+
+
+def test_lap3d_m64_DL_columns_match_time_stepper(sx):
+    """The non-normal variant D L at full size (every product entry formed, a = 1/||H||_F): eight
+    columns e^H e_j (interior, face, edge and corner nodes) against a Taylor time stepper on
+    cuSPARSE products, element-wise <= 1e-12 max_j ||e^H e_j||_1 of the sampled columns (a lower
+    bound of ||e^H||_1, so the bar is at least as strict as 1e-12 ||e^H||_1)."""
+    import torch
+    _free_cached()
+    c = get_config("lap3d_m64_DL")
+    H = c.build()
+    (rp, ci, v), st = sx.expm(torch_csr(H), c.tau, c.eps)
+    assert not st["normal"] and not st["symmetric"]
+    m = 64
+    cols = [0, m - 1, m * m * m - 1, 32 + 64 * 32 + 4096 * 32, 7 + 64 * 50 + 4096 * 20, 64 * 64 * 31, 4096 * 63 + 5,
+            int(np.random.default_rng(8).integers(0, H.n))]
+    R = torch.zeros(H.n, len(cols), dtype=torch.float64, device="cuda")
+    for k, j in enumerate(cols):
+        R[j, k] = 1.0
+    E = torch.sparse_csr_tensor(rp, ci.to(torch.int64), v, size=(H.n, H.n))
+    ER = torch.sparse.mm(E, R)
+    del E, rp, ci, v
+    _free_cached()
+    Hd = torch_csr(H)
+    Ht = torch.sparse_csr_tensor(Hd[0], Hd[1].to(torch.int64), Hd[2] * c.tau, size=(H.n, H.n))
+    Y = taylor_time_stepper(Ht, R, substeps=128)
+    n1 = float(Y.abs().sum(dim=0).max())
+    err = float((ER - Y).abs().max())
+    print(f"lap3d_m64_DL: M={st['M']} N={st['N']} nnz(e^H)={st['nnz_out']} max-abs={err:.2e} "
+          f"||cols||_1={n1:.3f} peak={st['peak_bytes'] / 2**30:.1f} GiB ms={st['ms_total']:.0f}")
+    assert err <= 1e-12 * n1
 
 
 def test_rgg_1e5_expm_times_R_matches_time_stepper(sx):

@@ -51,11 +51,11 @@ def _sprand(n, per_row, seed):
     return A
 
 
-def _ragged(n, seed, dense_rows=(), empty_rows=()):
+def _ragged(n, seed, dense_rows=(), empty_rows=(), dense_size=3000):
     rng = np.random.default_rng(seed + 1000)
     A = _sprand(n, min(6.0, n), seed).tolil()
     for r in dense_rows:
-        cols = rng.choice(n, size=min(n, 3000), replace=False)
+        cols = rng.choice(n, size=min(n, dense_size), replace=False)
         A[r, cols] = rng.uniform(-1, 1, size=len(cols))
     for r in empty_rows:
         A[r, :] = 0
@@ -80,8 +80,9 @@ def test_spgemm_taylor_term_matches_scipy(sx, n, seed):
 
 @pytest.mark.parametrize("n,seed,dense", [(64, 4, ()), (2000, 5, (3, 1500)), (40000, 6, (17, 20000, 39999))])
 def test_spgemm_squaring_matches_scipy(sx, n, seed, dense):
-    """T~ = 2T + T T (Eq. 4.15), including rows wide enough for the global-scratch class."""
-    T = _ragged(n, seed, dense_rows=dense, empty_rows=[1])
+    """T~ = 2T + T T (Eq. 4.15), including rows wide enough for the global-scratch class (rows of
+    30000 entries make product rows of nearly all 40000 columns: 320 KB of accumulators)."""
+    T = _ragged(n, seed, dense_rows=dense, empty_rows=[1], dense_size=30000)
     tt = torch_csr(_csr(T))
     (rp, ci, v), prod = sx.spgemm(tt, tt, tt, div=1.0, beta=2.0)
     G = to_scipy(rp, ci, v, n)
@@ -289,3 +290,47 @@ def test_expm_takes_and_returns_torch_sparse_csr(sx):
         assert torch.equal(E.crow_indices().cpu(), rp.cpu())
         assert torch.equal(E.col_indices().cpu(), ci.cpu().to(torch.int64))
         assert torch.equal(E.values().cpu(), v.cpu())
+
+
+# ------------------------------------------------------------------ chunked squaring
+
+def _chunk_case(variant):
+    if variant.startswith("lap3d"):
+        H = dirichlet_laplacian(12, 3)
+        if variant.endswith("DL"):
+            H, _ = diag_scale(H, seed=1)
+        return H, 2.1125 / 13 ** 2, 1e-12
+    c = get_config("lap2d_m32")
+    return c.build(), c.tau, c.eps
+
+
+@pytest.mark.parametrize("variant", ["lap3d", "lap3d_DL", "lap2d"])
+def test_chunked_squaring_matches_oracle(sx, variant):
+    """Squaring products formed in row chunks of at most 64 KB with Algorithm 4.1 streamed exactly
+    (entries below eps_g / (2 sqrt(nnz)) folded into one sum of squares): the 3-D grid (symmetric
+    mode, lower entries from earlier chunks' pieces), its non-normal D L variant (every entry
+    formed) and the 2-D grid, at the same parity bar against the oracle as the whole products."""
+    H, tau, eps = _chunk_case(variant)
+    res, st, so = _check_method(sx, H, tau, eps, chunk_bytes=65536)
+    sq = [r for r in st["steps"] if r["phase"] == 1]
+    assert max(r["chunks"] for r in sq) > 4
+    for r in sq:
+        if r["chunks"] > 1:
+            assert r["nnz"] <= r["nnz_stream"] <= r["nnz_raw"]
+    # the same decisions as the whole product up to the rounding of the sums: equal pass counts,
+    # thresholds within 1e-12 relative
+    (rp, ci, v), st_w = sx.expm(torch_csr(H), tau, eps)
+    for a, b in zip([r for r in st_w["steps"] if r["phase"] == 1], sq):
+        assert a["iters"] == b["iters"] and a["t"] == pytest.approx(b["t"], rel=1e-12)
+        assert a["nnz_raw"] == b["nnz_raw"]
+
+
+def test_spgemm_reaches_every_size_class(sx):
+    """The wide-row product of the squaring test really runs rows in the global-memory class (and in
+    the shared-memory classes): per-class row counts from the step record of sexpm_spgemm."""
+    T = _ragged(40000, 6, dense_rows=(17, 20000, 39999), empty_rows=[1], dense_size=30000)
+    tt = torch_csr(_csr(T))
+    rows = sx.spgemm_rows_per_class(tt, tt, tt, div=1.0, beta=2.0)
+    assert rows[5] >= 1, rows          # global-memory accumulators
+    assert rows[0] > 0, rows
+    assert 39000 < sum(rows) <= 40000, rows  # every non-empty product row is in exactly one class

@@ -101,3 +101,30 @@ def test_adjoint_pins_catch_a_missing_transpose(monkeypatch):
         r, c = np.searchsorted(Hc.indptr, p, side="right") - 1, Hc.indices[p]
         worst = max(worst, abs(G[r, c] - fd) / max(abs(fd), 1e-12))
     assert worst > 1e-3
+
+
+def test_oracle_adjoint_zero_branch_matches_first_order_term():
+    """At ||tau H|| = 0 the oracle's adjoint returns tau W on the pattern of H (the first-order term
+    of e^{tau H} = I + tau H + ...).  Pinned against central differences of the oracle's forward at
+    H = 0 along each stored entry (diagonal and off-diagonal): e^{tau d E_ij} = I + tau d E_ij
+    (i != j) or differs from I by e^{tau d} - 1 at (i, i)."""
+    import scipy.sparse as sp
+    n, tau, eps = 5, 0.7, 1e-14
+    rows = np.array([0, 1, 2, 3, 4, 4])
+    cols = np.array([0, 3, 2, 1, 0, 4])
+    H0 = sp.csr_matrix((np.zeros(6), (rows, cols)), shape=(n, n))
+    H0.sort_indices()
+    rng = np.random.default_rng(4)
+    W = sp.csr_matrix(rng.uniform(-1, 1, (n, n)))
+    G, E, st, tr = O.adjoint(H0, tau, eps, W)
+    G = sp.csr_matrix(G)
+    d = 1e-6
+    for i, j in zip(rows, cols):
+        def loss(x):
+            Hx = H0.copy().tolil()
+            Hx[i, j] = x
+            Ex, _ = O.expm(sp.csr_matrix(Hx), tau, eps)
+            return float(sp.csr_matrix(Ex).multiply(W).sum())
+        fd = (loss(d) - loss(-d)) / (2 * d)
+        assert G[i, j] == pytest.approx(tau * W[i, j], rel=1e-14)
+        assert fd == pytest.approx(G[i, j], rel=1e-8, abs=1e-12)
