@@ -145,6 +145,13 @@ def _oracle_sample(cfg_name: str, m_sample: int):
     return dt, H.shape[0], desc
 
 
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -161,13 +168,18 @@ def run_reference(args):
             times.append(dt)
     t = statistics.mean(times)
     value = (n_s / t) / n_full                            # rows of e^{tau H} per second, scaled to the full n
-    ncores = 1
+    ncores = 1                                            # scipy's sparse product runs on one thread
+    est = {"kind": "estimate: the timed sample's rate per row times the workload's rows",
+           "timed_n": n_s, "timed_ms_per_step": 1000.0 * t, "workload_n": n_full}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "expm/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value if value else None,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t,
+        "ms_per_step_is": "the timed sample's (n = %d), not the workload's" % n_s,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": c.desc},
-        "cpu_baseline": {"value": value, "unit": "expm/s", "cores": ncores, "kind": "oracle",
+        "config": {"workload": args.workload, "desc": c.desc, "timed_sample": desc},
+        "value_estimate": est,
+        "cpu_baseline": {"value": value, "unit": "expm/s", "cores": ncores, "host_cores": _host_cores(),
+                         "kind": "oracle", "estimate": est,
                          "sample": f"{desc}; {t:.2f} s per step; scaled by the row count to n={n_full} "
                                    f"(same per-row work for interior rows)"},
         "e2e": {"value": value, "unit": "expm/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -280,6 +292,84 @@ def measure_adjoint(sexpm, torch, fd_edges: int = 0):
     return out
 
 
+def measure_adjoint_trace(sexpm, torch, Hdev, c, n: int):
+    """Adjoint form on the bench workload: L = trace(P e^{tau H}) with a seeded diagonal P
+    (P_ii ~ U[0, 1], seed 4), i.e. dL/dE = P.  Times the kept forward (every product formed,
+    checkpoints every ceil(sqrt(N)) squarings) and the reverse pass (recomputing the iterates between
+    checkpoints), and the peak device memory the library held over both."""
+    import numpy as np
+    from workloads import diag_weights
+    P = diag_weights(n, seed=4)
+    W = (torch.arange(n + 1, dtype=torch.int64, device="cuda"), torch.arange(n, dtype=torch.int32, device="cuda"),
+         torch.from_numpy(P).cuda(), n)
+    plan = sexpm.Plan(Hdev, c.eps)
+    sexpm.release_memory()
+    live0, _ = sexpm.pool_stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tape, res = plan.forward_keep(c.tau)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    st = res.stats()
+    res.free()
+    rp, ci, g = tape.adjoint(W)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    live1, peak1 = sexpm.pool_stats()
+    tape.free()
+    plan.close()
+    gmax = float(g.abs().max()) if g.numel() else 0.0
+    del rp, ci, g
+    sexpm.release_memory()
+    return {"workload": "L = trace(P e^{tau H}), P_ii ~ U[0,1] (seed 4), on the bench workload",
+            "M": st["M"], "N": st["N"], "forward_keep_ms": 1000.0 * (t1 - t0), "reverse_ms": 1000.0 * (t2 - t1),
+            "adjoint_total_ms": 1000.0 * (t2 - t0), "peak_hbm_bytes": int(peak1 - live0), "max_abs_dL_dH": gmax}
+
+
+def error_vs_exact(sexpm, torch, plan, c, H, rows: int = 16):
+    """Max-abs error of sampled full rows of e^{tau H} against the closed form of the grid
+    Laplacian: e^{tau L_1} (x) e^{tau L_1} (x ...) with the 1-D sine eigenbasis.  None for other
+    workloads."""
+    import numpy as np
+    name = c.name.split("@")[0]
+    if not (name.startswith("lap2d_m") or name.startswith("lap3d_m")) or name.endswith("_DL"):
+        return None
+    dim = 2 if name.startswith("lap2d") else 3
+    m = int(round(H.n ** (1.0 / dim)))
+    h = 1.0 / (m + 1)
+    j = np.arange(1, m + 1)
+    lam = -(4.0 / h ** 2) * np.sin(j * np.pi * h / 2) ** 2
+    V = np.sqrt(2 * h) * np.sin(np.outer(j, j) * np.pi * h)
+    E1 = (V * np.exp(c.tau * lam)) @ V.T
+    res = plan.compute(c.tau)
+    try:
+        n_, nnz = res.info()
+        rp = np.empty(n_ + 1, dtype=np.int64)
+        import ctypes
+        sexpm._check(sexpm.load().sexpm_result_copy(res._h, rp.ctypes.data, None, None, 0))
+        rng = np.random.default_rng(11)
+        pick = sorted(set(int(x) for x in rng.integers(0, H.n, size=rows)) | {0, H.n - 1, H.n // 2})
+        ci_all, v_all = res.to_torch("cuda")[1:]
+        worst = 0.0
+        for i in pick:
+            a, b = int(rp[i]), int(rp[i + 1])
+            cols = ci_all[a:b].cpu().numpy()
+            vals = v_all[a:b].cpu().numpy()
+            if dim == 2:
+                exact = np.outer(E1[i // m], E1[i % m]).ravel()
+            else:
+                exact = np.einsum("a,b,c->abc", E1[i // (m * m)], E1[(i // m) % m], E1[i % m]).ravel()
+            got = np.zeros(H.n)
+            got[cols] = vals
+            worst = max(worst, float(np.abs(got - exact).max()))
+        del ci_all, v_all
+    finally:
+        res.free()
+    sexpm.release_memory()
+    return {"max_abs": worst, "rows_sampled": len(pick), "norm1_of_expm_at_most": 1.0,
+            "reference": "e^{tau L_1} Kronecker products from the 1-D sine eigenbasis (exact up to rounding)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -379,15 +469,24 @@ def run_ours(args):
         e2e = {"value": whole_job_rate(1000.0 * e2e_s, ws), "unit": "expm/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": int(statistics.mean(d2h_list)), "ms_per_step": 1000.0 * e2e_s}
 
+    err = None
     forms = None
-    if args.forms:
-        forms = {"adjoint": measure_adjoint(sexpm, torch, args.fd_edges), "batched": measure_batched(sexpm, torch)}
+    if rank == 0 and ws == 1:
+        err = error_vs_exact(sexpm, torch, plan, c, H)
+        if not args.no_forms:
+            forms = {"adjoint_trace": measure_adjoint_trace(sexpm, torch, dev, c, H.n),
+                     "adjoint_rgg": measure_adjoint(sexpm, torch, args.fd_edges)}
+        if args.forms:
+            forms = forms or {}
+            forms["batched"] = measure_batched(sexpm, torch)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         dt, n_s, desc = _oracle_sample(args.workload, args.sample_m)
         cpu_val = (n_s / dt) / H.n
-        cpu = {"value": cpu_val, "unit": "expm/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": cpu_val, "unit": "expm/s", "cores": 1, "host_cores": _host_cores(), "kind": "oracle",
+               "estimate": {"kind": "estimate: the timed sample's rate per row times the workload's rows",
+                            "timed_n": n_s, "timed_ms_per_step": 1000.0 * dt, "workload_n": H.n},
                "sample": f"{desc}; {dt:.2f} s; scaled by the row count to n={H.n} "
                          f"(same per-row work for interior rows)"}
 
@@ -423,6 +522,8 @@ def run_ours(args):
                           "numeric_gflops": round(r["flops"] / (r["ms_numeric"] * 1e6), 1) if r["ms_numeric"] else None}
                          for r in st["steps"]] if args.per_step else None,
             "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "forms": forms,
+            "error_vs_exact": err,
+            "chunked_steps": sum(1 for r in st["steps"] if r["chunks"] > 1),
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -430,7 +531,17 @@ def run_ours(args):
     return 0
 
 
+def _relaunch_with_ranks(n: int, argv) -> int:
+    """`bench.py --gpus N` started as one process: launch N ranks on this node (one per GPU) through
+    torch.distributed.run, as the multi-GPU launch does, and return its exit code."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", os.environ.get("SEXPM_BENCH_PORT", "29517"),
+           os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
+
+
 def main(argv=None):
+    argv = list(sys.argv[1:] if argv is None else argv)
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -446,10 +557,15 @@ def main(argv=None):
     ap.add_argument("--fd-edges", type=int, default=0,
                     help="with --forms: check the adjoint on this many random edges by finite differences")
     ap.add_argument("--forms", action="store_true",
-                    help="also time the batched form against the per-matrix loop (several minutes)")
+                    help="also time the batched form against the per-matrix loop and check the adjoint by "
+                         "finite differences (several minutes)")
     ap.add_argument("--sample-m", type=int, default=80,
                     help="grid side of the oracle's sample of the workload (same tau/h^2 and eps)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the adjoint timings that the default line carries")
     args = ap.parse_args(argv)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return _relaunch_with_ranks(args.gpus, argv)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -34,6 +34,11 @@
  *                       product row gives its warps private accumulators and
  *                       splits the k's of A_i among them (default 225280; 0 =
  *                       every warp owns a column range).  Read at every product.
+ * Environment (testing the error paths):
+ *   SEXPM_FAIL_ALLOC_AT=k  the k-th device allocation of each sexpm_compute fails
+ *                       on the host as if the device were out of memory
+ *                       (SEXPM_ENOMEM; everything allocated so far is released
+ *                       and the plan stays usable).  Read at every sexpm_compute.
  */
 #ifndef SEXPM_H_
 #define SEXPM_H_
@@ -51,7 +56,8 @@ extern "C" {
 #define SEXPM_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
 #define SEXPM_ENOCONV (-4)   /* Algorithm 4.1 hit its iteration cap */
 #define SEXPM_ENOPARAM (-5)  /* no feasible (M, N) in [N0, N0 + n_extra] */
-#define SEXPM_ETIMEOUT (-6)  /* a bounded device wait gave up */
+#define SEXPM_ETIMEOUT (-6)  /* a bounded device wait gave up (reserved: no call of this version
+                                waits on the device with a bound) */
 #define SEXPM_EOVERFLOW (-7) /* a size exceeded an index type or a fixed capacity */
 
 /* ------------------------------------------------------------------ types */

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <map>
@@ -64,8 +65,20 @@ cudaMemPool_t pool_for_current_device() {
 }
 }  // namespace
 
+// Host-side failure injection for tests of the error paths: when SEXPM_FAIL_ALLOC_AT=k is set
+// in the environment, the k-th pool allocation of every sexpm_compute fails as if the device
+// were out of memory (no device call is made for it).
+std::atomic<int64_t> g_fail_countdown{0};
+
+void arm_alloc_failure() {
+  const char* e = std::getenv("SEXPM_FAIL_ALLOC_AT");
+  g_fail_countdown.store(e && *e ? std::max<int64_t>(0, std::strtoll(e, nullptr, 10)) : 0);
+}
+
 void* Pool::alloc(size_t bytes, cudaStream_t s) {
   void* p = nullptr;
+  if (g_fail_countdown.load() > 0 && g_fail_countdown.fetch_sub(1) == 1)
+    fail(SEXPM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected by SEXPM_FAIL_ALLOC_AT)");
   cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool_for_current_device(), s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -980,6 +993,7 @@ int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
   *out = nullptr;
   if (p->count > 0) fail(SEXPM_EINVAL, "batched plan: use sexpm_compute_batched");
   sexpm_result* res = new sexpm_result();
+  arm_alloc_failure();
   try {
     compute_impl(p, tau, res, nullptr, p->opt.symmetric != 0);
   } catch (...) {

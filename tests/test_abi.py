@@ -123,3 +123,12 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     # machine without a GPU; never a result
     with pytest.raises((ImportError, RuntimeError)):
         sexpm.expm((np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([1.0]), 1), 1.0, 1e-12)
+
+
+def test_host_choose_MN_returns_enoparam_for_an_unreachable_tolerance(lib):
+    """No (M, N) in [N0, N0 + n_extra] with M <= max_M meets a tolerance far below what M terms
+    reach: SEXPM_ENOPARAM (-5), no output written."""
+    import ctypes
+    M, N = ctypes.c_int32(-9), ctypes.c_int32(-9)
+    rc = lib.sexpm_choose_MN(1e3, 1e-300, 0, 3, ctypes.byref(M), ctypes.byref(N))
+    assert rc == -5 and (M.value, N.value) == (-9, -9)

@@ -7,7 +7,7 @@ import pytest
 import scipy.sparse as sp
 
 from tests._compare import taylor_time_stepper, torch_csr
-from workloads import dirichlet_laplacian, get_config, rgg_adjacency, sparse_loss_weights
+from workloads import CSR, dirichlet_laplacian, get_config, rgg_adjacency, sparse_loss_weights
 
 pytestmark = pytest.mark.gpu
 
@@ -185,3 +185,79 @@ def test_rgg_1e5_adjoint_against_finite_differences(sx):
         assert abs(ad - fd) <= 1e-6 * max(abs(fd), abs(ad), 1e-3 * gmax), (u, w, ad, fd)
         checked += 1
     assert checked == 8
+
+
+def _diag_of(rp, ci, v, n):
+    """Diagonal of a device CSR (torch tensors), 0 where absent."""
+    import torch
+    rows = torch.repeat_interleave(torch.arange(n, dtype=torch.int32, device=rp.device), rp[1:] - rp[:-1])
+    on = ci == rows
+    d = torch.zeros(n, dtype=torch.float64, device=rp.device)
+    d[rows[on].long()] = v[on]
+    return d
+
+
+def test_lap2d_m1500_adjoint_of_trace(sx):
+    """The bench workload's adjoint (n = 2.25M): L = trace(P e^{tau H}) through one kept forward
+    (sexpm_forward_keep, checkpoints every ceil(sqrt(N)) squarings) and two reverse passes.
+    P = I: dL/dH = (e^{tau H})^T on the pattern of H, every stored entry against the Kronecker
+    closed form.  P seeded diagonal (P_ii ~ U[0,1], seed 4): central differences of the GPU
+    forward along two diagonal entries and two symmetric off-diagonal pairs, relative error
+    <= 1e-6 with no floor."""
+    import torch
+    from workloads import diag_weights
+    _free_cached()
+    c = get_config("lap2d_m1500")
+    H = c.build()
+    n, m = H.n, 1500
+    plan = sx.Plan(torch_csr(H), c.eps)
+    tape, res = plan.forward_keep(c.tau)
+    st = res.stats()
+    res.free()
+    ar = lambda k, dt: torch.arange(k, dtype=dt, device="cuda")
+    _, _, g_I = tape.adjoint((ar(n + 1, torch.int64), ar(n, torch.int32), torch.ones(n, dtype=torch.float64,
+                                                                                     device="cuda"), n))
+    P = diag_weights(n, seed=4)
+    _, _, g_P = tape.adjoint((ar(n + 1, torch.int64), ar(n, torch.int32), torch.from_numpy(P).cuda(), n))
+    live, peak = sx.pool_stats()
+    tape.free()
+    plan.close()
+    g_I, g_P = g_I.cpu().numpy(), g_P.cpu().numpy()
+    E1 = _sine_basis_expm(m, c.tau)
+    rows = np.repeat(np.arange(n), np.diff(H.row_ptr))
+    cols = H.col.astype(np.int64)
+    exact = E1[rows // m, cols // m] * E1[rows % m, cols % m]
+    err_I = float(np.abs(g_I - exact).max())
+    print(f"adjoint trace: M={st['M']} N={st['N']} |dL/dH - (e^H)^T| max={err_I:.2e} "
+          f"peak over forward+reverse={peak / 2**30:.1f} GiB")
+    assert err_I <= 1e-11 * float(np.abs(exact).max())
+
+    Pd = torch.from_numpy(P).cuda()
+
+    def loss(vals):
+        (erp, eci, ev), _ = sx.expm(torch_csr(CSR(n, H.row_ptr, H.col, vals)), c.tau, c.eps)
+        out = float((_diag_of(erp, eci, ev, n) * Pd).sum())
+        del erp, eci, ev
+        _free_cached()
+        return out
+
+    rng = np.random.default_rng(12)
+    picks = []
+    for i in rng.integers(0, n, size=2):
+        p = H.row_ptr[i] + np.searchsorted(H.col[H.row_ptr[i]:H.row_ptr[i + 1]], i)
+        picks.append(("diag", [int(p)]))
+    for i in rng.integers(m, n - m, size=2):
+        p = H.row_ptr[i] + np.searchsorted(H.col[H.row_ptr[i]:H.row_ptr[i + 1]], i + m)
+        q = H.row_ptr[i + m] + np.searchsorted(H.col[H.row_ptr[i + m]:H.row_ptr[i + m + 1]], i)
+        picks.append(("pair", [int(p), int(q)]))
+    for kind, ps in picks:
+        d = 1e-4 * abs(H.val[ps[0]])  # the step in H (e^{tau H}: tau H moves by 1e-4 tau |H_p|)
+        vp, vm = H.val.copy(), H.val.copy()
+        for p in ps:
+            vp[p] += d
+            vm[p] -= d
+        fd = (loss(vp) - loss(vm)) / (2 * d)
+        ad = float(sum(g_P[p] for p in ps))
+        rel = abs(ad - fd) / abs(fd)
+        print(f"  FD {kind} entries {ps}: adjoint {ad:.12e} fd {fd:.12e} rel {rel:.2e}")
+        assert rel <= 1e-6
