@@ -275,6 +275,19 @@ int sexpm_spgemm(const sexpm_csr_view* A, const sexpm_csr_view* B, const sexpm_c
 int sexpm_filter(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_iters, void* stream,
                  sexpm_result_t** out, double* t, int32_t* iters, double* b);
 
+/* One Algorithm 4.1 reduction pass on the stored values of A (device or host view): the sum of
+ * v^2 over the entries with |v| <= t (*sum_dropped) and the number of entries with |v| > t
+ * (*kept).  With the threshold sequence t_0 = eps_g, t_{j+1} = eps_g t_j / b_j driven by the caller,
+ * this is the pass a multi-process run all-reduces across its row blocks.  t >= 0. */
+int sexpm_filter_pass(const sexpm_csr_view* A, double t, void* stream, double* sum_dropped, int64_t* kept);
+
+/* A~ = A - b_n of Algorithm 4.1 at a given final threshold: the entries of A with |v| > t. */
+int sexpm_filter_apply(const sexpm_csr_view* A, double t, void* stream, sexpm_result_t** out);
+
+/* sum over the rows r0 <= i < r1 of A of sum_j (delta_ij + a_ij)^2, the part of ||I + A||_F^2
+ * (the relative threshold of the squaring steps, Sec. 4.2) that those rows hold. */
+int sexpm_norm2_I_plus_rows(const sexpm_csr_view* A, int64_t r0, int64_t r1, void* stream, double* out);
+
 /* ------------------------------------------------------- no-allocation call */
 
 /* Largest number of rows sexpm_filter_noalloc accepts (its fixed scratch size). */

@@ -1117,6 +1117,85 @@ int sexpm_filter(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_
   SX_API_END
 }
 
+int sexpm_filter_pass(const sexpm_csr_view* A, double t, void* stream, double* sum_dropped, int64_t* kept) {
+  SX_API_BEGIN
+  if (!A || !sum_dropped) fail(SEXPM_EINVAL, "null argument");
+  if (!(t >= 0.0)) fail(SEXPM_EINVAL, "t must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostScalars hs;
+  CsrOwned a;
+  upload(*A, s, a, hs);
+  Piece p;
+  p.r1 = a.n;
+  p.nnz = a.nnz;
+  p.rp = a.rp.p;
+  p.ci = a.ci.p;
+  p.v = a.v.p;
+  std::vector<Piece> P{p};
+  std::vector<int64_t> base{0, tiles_of(a.nnz)};
+  DevBuf<int32_t> tc(base[1] ? base[1] : 1, s);
+  *sum_dropped = pass_pieces(P, base, t, tc.p, s, hs);
+  if (kept) {
+    DevBuf<int64_t> off(base[1] + 1, s);
+    *kept = scan_counts(tc.p, base[1], off.p, s, hs);
+  }
+  SX_API_END
+}
+
+int sexpm_filter_apply(const sexpm_csr_view* A, double t, void* stream, sexpm_result_t** out) {
+  SX_API_BEGIN
+  if (!A || !out) fail(SEXPM_EINVAL, "null argument");
+  *out = nullptr;
+  if (!(t >= 0.0)) fail(SEXPM_EINVAL, "t must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostScalars hs;
+  CsrOwned a;
+  upload(*A, s, a, hs);
+  sexpm_result* res = new sexpm_result();
+  try {
+    res->s = s;
+    std::memset(&res->st, 0, sizeof(res->st));
+    Piece p;
+    p.r1 = a.n;
+    p.nnz = a.nnz;
+    p.rp = a.rp.p;
+    p.ci = a.ci.p;
+    p.v = a.v.p;
+    std::vector<Piece> P{p};
+    std::vector<int64_t> base{0, tiles_of(a.nnz)};
+    DevBuf<int32_t> tc(base[1] ? base[1] : 1, s);
+    pass_pieces(P, base, t, tc.p, s, hs);
+    res->E.n = a.n;
+    res->E.rp.reset(a.n + 1, s);
+    DevBuf<int64_t> off(base[1] + 1, s);
+    res->E.nnz = scan_counts(tc.p, base[1], off.p, s, hs);
+    res->E.ci.reset(res->E.nnz, s);
+    res->E.v.reset(res->E.nnz, s);
+    if (a.n == 0) SX_CUDA(cudaMemsetAsync(res->E.rp.p, 0, sizeof(int64_t), s));
+    else compact_pieces(P, base, t, off.p, a.n, res->E, s);
+    SX_CUDA(cudaStreamSynchronize(s));
+    res->st.n = res->E.n;
+    res->st.nnz_out = res->E.nnz;
+  } catch (...) {
+    delete res;
+    throw;
+  }
+  *out = res;
+  SX_API_END
+}
+
+int sexpm_norm2_I_plus_rows(const sexpm_csr_view* A, int64_t r0, int64_t r1, void* stream, double* out) {
+  SX_API_BEGIN
+  if (!A || !out) fail(SEXPM_EINVAL, "null argument");
+  if (r0 < 0 || r1 < r0 || r1 > A->n) fail(SEXPM_EINVAL, "row range outside the matrix");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostScalars hs;
+  CsrOwned a;
+  upload(*A, s, a, hs);
+  *out = norm2_I_plus_rows(a.view(), r0, r1, s, hs);
+  SX_API_END
+}
+
 int sexpm_plan_batched(const sexpm_csr_view* Hs, int32_t count, double eps, const sexpm_options* opt, void* stream,
                        sexpm_plan_t** out) {
   SX_API_BEGIN

@@ -388,7 +388,48 @@ __global__ void __launch_bounds__(256) k_compact_rows(int64_t r0, int64_t r1, co
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// part[block] = sum over the block's rows r0 <= i < r1 of sum_j (delta_ij + a_ij)^2 (one warp per row).
+__global__ void k_norm2_I_plus_rows(CsrD A, int64_t r0, int64_t r1, double* part) {
+  __shared__ double red[8];
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  double s = 0.0;
+  for (int64_t i = r0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < r1; i += nw) {
+    bool diag = false;
+    for (int64_t p = A.rp[i] + lane_id(); p < A.rp[i + 1]; p += 32) {
+      const double x = A.v[p];
+      if (A.ci[p] == (int)i) {
+        diag = true;
+        s = fma(1.0 + x, 1.0 + x, s);
+      } else {
+        s = fma(x, x, s);
+      }
+    }
+    if (!__any_sync(FULL, diag) && lane_id() == 0) s += 1.0;
+  }
+  s = warp_sum(s);
+  if (lane_id() == 0) red[warp_id()] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
 }  // namespace
+
+double norm2_I_plus_rows(const CsrD& A, int64_t r0, int64_t r1, cudaStream_t s, HostScalars& hs) {
+  if (r1 <= r0) return 0.0;
+  const int grid = (int)std::min<int64_t>(kRowBlocks, (r1 - r0 + 7) / 8);
+  DevBuf<double> part(grid + 1, s);
+  k_norm2_I_plus_rows<<<grid, 256, 0, s>>>(A, r0, r1, part.p);
+  k_sum_parts<<<1, 1024, 0, s>>>(part.p, grid, part.p + grid);
+  SX_CUDA(cudaGetLastError());
+  count_launches(2);
+  SX_CUDA(cudaMemcpyAsync(hs.d, part.p + grid, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SX_CUDA(cudaStreamSynchronize(s));
+  return hs.d[0];
+}
 
 // ---------------------------------------------------------------- host side
 

@@ -259,6 +259,8 @@ void compact_pieces(const std::vector<Piece>& P, const std::vector<int64_t>& til
 // mirror's value and decision (same chunk, or the earlier device pieces).  Synchronises s.
 double drop_rows(int64_t r0, int64_t r1, const int64_t* rp, int64_t base, const int32_t* ci, double* v, bool sym,
                  double L, const Piece* pieces, int npieces, int32_t* keep, cudaStream_t s, HostScalars& hs);
+// sum over the rows r0 <= i < r1 of sum_j (delta_ij + a_ij)^2.  Synchronises s.
+double norm2_I_plus_rows(const CsrD& A, int64_t r0, int64_t r1, cudaStream_t s, HostScalars& hs);
 // Copies the entries drop_rows kept into a piece (out_rp: scanned keep, r1 - r0 + 1 entries).
 void compact_rows(int64_t r0, int64_t r1, const int64_t* rp, int64_t base, const int32_t* ci, const double* v, bool sym,
                   double L, const int64_t* out_rp, int32_t* out_ci, double* out_v, cudaStream_t s);

@@ -99,6 +99,9 @@ def load() -> ctypes.CDLL:
     L.sexpm_compute_batched.argtypes = [vp, P(ctypes.c_double), P(vp)]
     L.sexpm_adjoint.argtypes = [vp, ctypes.c_double, P(CsrView), ctypes.c_int32, P(vp), P(vp)]
     L.sexpm_forward_keep.argtypes = [vp, ctypes.c_double, ctypes.c_int32, P(vp), P(vp)]
+    L.sexpm_filter_pass.argtypes = [P(CsrView), ctypes.c_double, vp, P(ctypes.c_double), P(ctypes.c_int64)]
+    L.sexpm_filter_apply.argtypes = [P(CsrView), ctypes.c_double, vp, P(vp)]
+    L.sexpm_norm2_I_plus_rows.argtypes = [P(CsrView), ctypes.c_int64, ctypes.c_int64, vp, P(ctypes.c_double)]
     L.sexpm_adjoint_tape.argtypes = [vp, P(CsrView), P(vp)]
     L.sexpm_tape_free.argtypes = [vp]
     L.sexpm_tape_free.restype = None
@@ -453,6 +456,37 @@ def filter_csr(A, eps_g: float, e_r: float = 0.1, max_iters: int = 100, device="
         return res.to_torch(device), t.value, it.value, b.value
     finally:
         res.free()
+
+
+def filter_pass(A, t: float) -> Tuple[float, int]:
+    """One Algorithm 4.1 pass (sexpm_filter_pass): (sum of v^2 over |v| <= t, entries with |v| > t)."""
+    keep: List[Any] = []
+    a = _make_view(A, keep)
+    sd, kept = ctypes.c_double(), ctypes.c_int64()
+    _check(load().sexpm_filter_pass(ctypes.byref(a), float(t), _stream_ptr(), ctypes.byref(sd), ctypes.byref(kept)))
+    return sd.value, kept.value
+
+
+def filter_apply(A, t: float, device="cuda"):
+    """The entries of A with |v| > t (sexpm_filter_apply) as (row_ptr, col, val) torch tensors."""
+    keep: List[Any] = []
+    a = _make_view(A, keep)
+    r = ctypes.c_void_p()
+    _check(load().sexpm_filter_apply(ctypes.byref(a), float(t), _stream_ptr(), ctypes.byref(r)))
+    res = Result(r.value)
+    try:
+        return res.to_torch(device)
+    finally:
+        res.free()
+
+
+def norm2_I_plus_rows(A, r0: int, r1: int) -> float:
+    """sum over rows r0..r1-1 of sum_j (delta_ij + a_ij)^2 (sexpm_norm2_I_plus_rows)."""
+    keep: List[Any] = []
+    a = _make_view(A, keep)
+    out = ctypes.c_double()
+    _check(load().sexpm_norm2_I_plus_rows(ctypes.byref(a), int(r0), int(r1), _stream_ptr(), ctypes.byref(out)))
+    return out.value
 
 
 NOALLOC_MAX_ROWS = 1048576

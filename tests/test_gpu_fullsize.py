@@ -1,6 +1,7 @@
 """Checks at the full sizes of the benchmark workloads, where the CPU oracle cannot run:
 sampled outputs against closed forms, and e^H R against an independent time stepper."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -91,11 +92,14 @@ def test_lap3d_m64_rows_match_kronecker_closed_form(sx):
     _free_cached()
 
 
-def test_lap3d_m64_DL_columns_match_time_stepper(sx):
-    """The non-normal variant D L at full size (every product entry formed, a = 1/||H||_F): eight
-    columns e^H e_j (interior, face, edge and corner nodes) against a Taylor time stepper on
-    cuSPARSE products, element-wise <= 1e-12 max_j ||e^H e_j||_1 of the sampled columns (a lower
-    bound of ||e^H||_1, so the bar is at least as strict as 1e-12 ||e^H||_1)."""
+@pytest.mark.skipif(os.environ.get("SEXPM_FULLSIZE_DL") != "1",
+                    reason="about 17 minutes on one GB300; run with SEXPM_FULLSIZE_DL=1")
+def test_lap3d_m64_DL_rows_match_time_stepper(sx):
+    """The non-normal variant D L at full size (every product entry formed, a = 1/||H||_F, the
+    last squarings in row chunks): eight full rows e_j^T e^H (interior, face, edge and corner
+    nodes) against a Taylor time stepper for e^{tau H^T} e_j on cuSPARSE products,
+    element-wise <= 1e-12 max_j ||e_j^T e^H||_1 (a lower bound of ||e^H||_inf, the bar of the
+    transposed problem)."""
     import torch
     _free_cached()
     c = get_config("lap3d_m64_DL")
@@ -103,22 +107,28 @@ def test_lap3d_m64_DL_columns_match_time_stepper(sx):
     (rp, ci, v), st = sx.expm(torch_csr(H), c.tau, c.eps)
     assert not st["normal"] and not st["symmetric"]
     m = 64
-    cols = [0, m - 1, m * m * m - 1, 32 + 64 * 32 + 4096 * 32, 7 + 64 * 50 + 4096 * 20, 64 * 64 * 31, 4096 * 63 + 5,
+    rows = [0, m - 1, m * m * m - 1, 32 + 64 * 32 + 4096 * 32, 7 + 64 * 50 + 4096 * 20, 64 * 64 * 31, 4096 * 63 + 5,
             int(np.random.default_rng(8).integers(0, H.n))]
-    R = torch.zeros(H.n, len(cols), dtype=torch.float64, device="cuda")
-    for k, j in enumerate(cols):
-        R[j, k] = 1.0
-    E = torch.sparse_csr_tensor(rp, ci.to(torch.int64), v, size=(H.n, H.n))
-    ER = torch.sparse.mm(E, R)
-    del E, rp, ci, v
+    got = np.zeros((H.n, len(rows)))
+    for k, (cols, vals) in enumerate(_rows(rp, ci, v, rows)):
+        got[cols, k] = vals
+    del rp, ci, v
     _free_cached()
-    Hd = torch_csr(H)
-    Ht = torch.sparse_csr_tensor(Hd[0], Hd[1].to(torch.int64), Hd[2] * c.tau, size=(H.n, H.n))
-    Y = taylor_time_stepper(Ht, R, substeps=128)
-    n1 = float(Y.abs().sum(dim=0).max())
-    err = float((ER - Y).abs().max())
+    Ht_s = sp.csr_matrix(H.to_scipy().T)
+    Ht_s.sort_indices()
+    Ht = torch.sparse_csr_tensor(torch.from_numpy(Ht_s.indptr.astype(np.int64)).cuda(),
+                                 torch.from_numpy(Ht_s.indices.astype(np.int64)).cuda(),
+                                 torch.from_numpy(Ht_s.data * c.tau).cuda(), size=(H.n, H.n))
+    R = torch.zeros(H.n, len(rows), dtype=torch.float64, device="cuda")
+    for k, j in enumerate(rows):
+        R[j, k] = 1.0
+    Y = taylor_time_stepper(Ht, R, substeps=128).cpu().numpy()
+    n1 = float(np.abs(Y).sum(axis=0).max())
+    err = float(np.abs(got - Y).max())
+    sq = [r for r in st["steps"] if r["phase"] == 1]
     print(f"lap3d_m64_DL: M={st['M']} N={st['N']} nnz(e^H)={st['nnz_out']} max-abs={err:.2e} "
-          f"||cols||_1={n1:.3f} peak={st['peak_bytes'] / 2**30:.1f} GiB ms={st['ms_total']:.0f}")
+          f"||rows||_1={n1:.3f} peak={st['peak_bytes'] / 2**30:.1f} GiB ms={st['ms_total']:.0f} "
+          f"chunks={[r['chunks'] for r in sq]}")
     assert err <= 1e-12 * n1
 
 
