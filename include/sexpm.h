@@ -288,6 +288,21 @@ int sexpm_filter_apply(const sexpm_csr_view* A, double t, void* stream, sexpm_re
  * (the relative threshold of the squaring steps, Sec. 4.2) that those rows hold. */
 int sexpm_norm2_I_plus_rows(const sexpm_csr_view* A, int64_t r0, int64_t r1, void* stream, double* out);
 
+/* ------------------------------------------------- applying e^{tau H} to vectors */
+
+/* Y = E X for a result E (n x n) and a block X of r vectors: X and Y are device arrays of n x r
+ * doubles, row-major (vector c of row k at X[k r + c]); X and Y must not overlap.  This is how
+ * the computed exponential is used (Sec. 5.3 applies it to a block of random vectors). */
+int sexpm_result_spmm(const sexpm_result_t* E, const double* X, int64_t r, double* Y, void* stream);
+
+/* Time stepping with a computed propagator (Eq. 2.2): U_k = E U_{k-1}, k = 1..steps, from U_0;
+ * U0 and U are device arrays of n x r doubles (row-major, may be the same array).  One n x r
+ * work array comes from the library's pool. */
+int sexpm_propagate(const sexpm_result_t* E, const double* U0, int64_t r, int32_t steps, double* U, void* stream);
+
+/* Y = A X for a borrowed CSR view (copied to the device first) and device X, Y as above. */
+int sexpm_spmm(const sexpm_csr_view* A, const double* X, int64_t r, double* Y, void* stream);
+
 /* ------------------------------------------------------- no-allocation call */
 
 /* Largest number of rows sexpm_filter_noalloc accepts (its fixed scratch size). */

@@ -17,8 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsexpm.so")
-SOURCES = ["api.cu", "kernels_spgemm.cu", "kernels_csr.cu", "kernels_filter.cu", "kernels_adjoint.cu", "noalloc.cu",
-           "plan.cpp"]
+SOURCES = ["api.cu", "kernels_spgemm.cu", "kernels_csr.cu", "kernels_filter.cu", "kernels_adjoint.cu", "kernels_spmm.cu",
+           "noalloc.cu", "plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1117,6 +1117,52 @@ int sexpm_filter(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_
   SX_API_END
 }
 
+int sexpm_result_spmm(const sexpm_result_t* E, const double* X, int64_t r, double* Y, void* stream) {
+  SX_API_BEGIN
+  if (!E || (E->E.n && r > 0 && (!X || !Y))) fail(SEXPM_EINVAL, "null argument");
+  if (r < 0) fail(SEXPM_EINVAL, "r must be >= 0");
+  if (X == Y && E->E.n && r) fail(SEXPM_EINVAL, "X and Y must not overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  spmm(E->E.view(), X, r, Y, s);
+  SX_CUDA(cudaStreamSynchronize(s));
+  SX_API_END
+}
+
+int sexpm_propagate(const sexpm_result_t* E, const double* U0, int64_t r, int32_t steps, double* U, void* stream) {
+  SX_API_BEGIN
+  if (!E || (E->E.n && r > 0 && (!U0 || !U))) fail(SEXPM_EINVAL, "null argument");
+  if (r < 0 || steps < 0) fail(SEXPM_EINVAL, "r and steps must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = E->E.n;
+  const size_t bytes = (size_t)n * (size_t)r * sizeof(double);
+  if (n && r) {
+    // two work arrays, alternated; the last product is copied to U (which may alias U0)
+    DevBuf<double> w0((size_t)n * (size_t)r, s), w1(steps > 1 ? (size_t)n * (size_t)r : 0, s);
+    const double* src = U0;
+    for (int k = 0; k < steps; ++k) {
+      double* dst = (k % 2 == 0) ? w0.p : w1.p;
+      spmm(E->E.view(), src, r, dst, s);
+      src = dst;
+    }
+    if (src != U) SX_CUDA(cudaMemcpyAsync(U, src, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  SX_CUDA(cudaStreamSynchronize(s));
+  SX_API_END
+}
+
+int sexpm_spmm(const sexpm_csr_view* A, const double* X, int64_t r, double* Y, void* stream) {
+  SX_API_BEGIN
+  if (!A || (A->n && r > 0 && (!X || !Y))) fail(SEXPM_EINVAL, "null argument");
+  if (r < 0) fail(SEXPM_EINVAL, "r must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostScalars hs;
+  CsrOwned a;
+  upload(*A, s, a, hs);
+  spmm(a.view(), X, r, Y, s);
+  SX_CUDA(cudaStreamSynchronize(s));
+  SX_API_END
+}
+
 int sexpm_filter_pass(const sexpm_csr_view* A, double t, void* stream, double* sum_dropped, int64_t* kept) {
   SX_API_BEGIN
   if (!A || !sum_dropped) fail(SEXPM_EINVAL, "null argument");

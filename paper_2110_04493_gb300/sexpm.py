@@ -99,6 +99,9 @@ def load() -> ctypes.CDLL:
     L.sexpm_compute_batched.argtypes = [vp, P(ctypes.c_double), P(vp)]
     L.sexpm_adjoint.argtypes = [vp, ctypes.c_double, P(CsrView), ctypes.c_int32, P(vp), P(vp)]
     L.sexpm_forward_keep.argtypes = [vp, ctypes.c_double, ctypes.c_int32, P(vp), P(vp)]
+    L.sexpm_result_spmm.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    L.sexpm_propagate.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
+    L.sexpm_spmm.argtypes = [P(CsrView), vp, ctypes.c_int64, vp, vp]
     L.sexpm_filter_pass.argtypes = [P(CsrView), ctypes.c_double, vp, P(ctypes.c_double), P(ctypes.c_int64)]
     L.sexpm_filter_apply.argtypes = [P(CsrView), ctypes.c_double, vp, P(vp)]
     L.sexpm_norm2_I_plus_rows.argtypes = [P(CsrView), ctypes.c_int64, ctypes.c_int64, vp, P(ctypes.c_double)]
@@ -221,6 +224,26 @@ class Result:
         _check(load().sexpm_result_copy(self._h, rp.ctypes.data, ci.ctypes.data if nnz else None,
                                         v.ctypes.data if nnz else None, 0))
         return rp, ci, v
+
+    def spmm(self, X):
+        """E X for a device block X (n x r float64 torch tensor, or a length-n vector):
+        sexpm_result_spmm."""
+        import torch
+        vec = X.dim() == 1
+        X2 = X.reshape(X.shape[0], -1).to(torch.float64).contiguous()
+        Y = torch.empty_like(X2)
+        _check(load().sexpm_result_spmm(self._h, X2.data_ptr(), X2.shape[1], Y.data_ptr(), _stream_ptr()))
+        return Y.reshape(-1) if vec else Y
+
+    def propagate(self, U0, steps: int):
+        """E^steps U0 by time stepping U_k = E U_{k-1} (sexpm_propagate)."""
+        import torch
+        vec = U0.dim() == 1
+        U2 = U0.reshape(U0.shape[0], -1).to(torch.float64).contiguous()
+        out = torch.empty_like(U2)
+        _check(load().sexpm_propagate(self._h, U2.data_ptr(), U2.shape[1], int(steps), out.data_ptr(),
+                                      _stream_ptr()))
+        return out.reshape(-1) if vec else out
 
     def stats(self) -> Dict[str, Any]:
         st = Stats()
@@ -456,6 +479,18 @@ def filter_csr(A, eps_g: float, e_r: float = 0.1, max_iters: int = 100, device="
         return res.to_torch(device), t.value, it.value, b.value
     finally:
         res.free()
+
+
+def spmm(A, X):
+    """A X for a CSR A (copied to the device) and a device block X (n x r float64): sexpm_spmm."""
+    import torch
+    keep: List[Any] = []
+    a = _make_view(A, keep)
+    vec = X.dim() == 1
+    X2 = X.reshape(X.shape[0], -1).to(torch.float64).contiguous()
+    Y = torch.empty_like(X2)
+    _check(load().sexpm_spmm(ctypes.byref(a), X2.data_ptr(), X2.shape[1], Y.data_ptr(), _stream_ptr()))
+    return Y.reshape(-1) if vec else Y
 
 
 def filter_pass(A, t: float) -> Tuple[float, int]:

@@ -132,69 +132,107 @@ def test_lap3d_m64_DL_rows_match_time_stepper(sx):
     assert err <= 1e-12 * n1
 
 
-def test_rgg_1e5_expm_times_R_matches_time_stepper(sx):
-    """The differentiation workload's forward (RGG n = 1e5, H = 0.5 A, eps = 1e-12): e^H R for
-    four seeded vectors against a Taylor time stepper built on cuSPARSE SpMM (64 substeps,
-    terms until they fall below 1e-20 of the running sum)."""
+def test_rgg_1e5_columns_match_time_stepper(sx):
+    """The differentiation workload's forward (RGG n = 1e5, H = 0.5 A, eps = 1e-12): sixteen
+    columns e^H e_j (through sexpm_result_spmm) element-wise against a Taylor time stepper built
+    on cuSPARSE products (64 substeps, terms until they fall below 1e-20 of the running sum), at
+    1e-12 max_j ||e^H e_j||_1 (a lower bound of ||e^H||_1); and e^H R for four random vectors."""
     import torch
     A = rgg_adjacency(100_000, seed=3)
     Hv = 0.5 * A.val
     Hd = (torch.from_numpy(A.row_ptr).cuda(), torch.from_numpy(A.col).cuda(), torch.from_numpy(Hv).cuda(), A.n)
-    (rp, ci, v), st = sx.expm(Hd, 1.0, 1e-12)
-    E = torch.sparse_csr_tensor(rp, ci.to(torch.int64), v, size=(A.n, A.n))
+    plan = sx.Plan(Hd, 1e-12)
+    E = plan.compute(1.0)
+    cols = np.random.default_rng(7).choice(A.n, size=16, replace=False)
+    R = torch.zeros(A.n, 20, dtype=torch.float64, device="cuda")
+    for k, j in enumerate(cols):
+        R[j, k] = 1.0
+    R[:, 16:] = torch.from_numpy(np.random.default_rng(7).uniform(-1, 1, (A.n, 4))).cuda()
+    ER = E.spmm(R)
+    E.free()
+    plan.close()
     Ht = torch.sparse_csr_tensor(Hd[0], Hd[1].to(torch.int64), Hd[2], size=(A.n, A.n))
-    R = torch.from_numpy(np.random.default_rng(7).uniform(-1, 1, (A.n, 4))).cuda()
-    Y = R.clone()
-    steps = 64
-    for _ in range(steps):
-        term, acc = Y.clone(), Y.clone()
-        for k in range(1, 60):
-            term = torch.sparse.mm(Ht, term) / (steps * k)
-            acc = acc + term
-            if term.abs().max() <= 1e-20 * acc.abs().max():
-                break
-        Y = acc
-    ER = torch.sparse.mm(E, R)
-    err = (ER - Y).abs().max().item() / Y.abs().max().item()
-    assert err <= 1e-11
+    Y = taylor_time_stepper(Ht, R, substeps=64)
+    n1 = float(Y[:, :16].abs().sum(dim=0).max())
+    err_cols = float((ER[:, :16] - Y[:, :16]).abs().max())
+    err_R = float((ER[:, 16:] - Y[:, 16:]).abs().max() / Y[:, 16:].abs().max())
+    print(f"rgg_1e5 forward: columns max-abs {err_cols:.2e} (||cols||_1 {n1:.3f}); e^H R rel {err_R:.2e}")
+    assert err_cols <= 1e-12 * n1
+    assert err_R <= 1e-12
+
+
+def _gather_loss_fn(W, n):
+    """L(E) = sum_ij W_ij E_ij for a device CSR E, by locating W's entries in E's sorted keys."""
+    import torch
+    Ws = W.to_scipy().tocoo()
+    wk = torch.from_numpy(Ws.row.astype(np.int64) * n + Ws.col.astype(np.int64)).cuda()
+    wv = torch.from_numpy(Ws.data.astype(np.float64)).cuda()
+
+    def loss(rp, ci, v, absolute=False):
+        rows = torch.repeat_interleave(torch.arange(n, device="cuda"), rp[1:] - rp[:-1])
+        keys = rows * n + ci.to(torch.int64)
+        pos = torch.searchsorted(keys, wk).clamp(max=keys.numel() - 1)
+        hit = keys[pos] == wk
+        vals = torch.where(hit, v[pos], torch.zeros_like(wv))
+        return float((wv.abs() * vals.abs()).sum()) if absolute else float((wv * vals).sum())
+
+    return loss
 
 
 def test_rgg_1e5_adjoint_against_finite_differences(sx):
-    """dL/dA_e = 0.5 (dL/dH_uv + dL/dH_vu) on 8 random edges of the 1e5-node graph against
-    central differences of the GPU forward: relative error <= 1e-6, measured against
-    max(|fd|, 1e-3 max|dL/dH|) (below that the difference quotient's rounding noise,
-    ~1e-16 |L| / delta, dominates)."""
+    """dL/dw_e = 0.5 (dL/dH_uv + dL/dH_vu) for L = <W, e^H> on the 1e5-node graph against central
+    differences of the GPU forward on 64 random edges, each with its plain relative error
+    |adjoint - fd| / |fd| <= 1e-6 (no floor).  A difference quotient resolves a gradient only
+    above its rounding noise, about 2^-52 sum|W_ij E_ij| / delta; the 64 edges are drawn from the
+    edges whose adjoint gradient is at least 1e6 times that noise (a 1e-6 relative check is
+    meaningful there), and the share of edges below it is printed: W has 1e5 entries at random
+    positions, so most edges lie too far from every one of them to have a resolvable gradient."""
     import torch
     A = rgg_adjacency(100_000, seed=3)
-    W = sparse_loss_weights(A.n, 100_000, seed=3)
-    Ws = W.to_scipy()
+    n = A.n
+    W = sparse_loss_weights(n, 100_000, seed=3)
     dev = lambda vals: (torch.from_numpy(A.row_ptr).cuda(), torch.from_numpy(A.col).cuda(),
-                        torch.from_numpy(vals).cuda(), A.n)
+                        torch.from_numpy(vals).cuda(), n)
     rp, ci, g = sx.adjoint(dev(0.5 * A.val), 1.0, 1e-12, torch_csr(W))
-    G = sp.csr_matrix((g.cpu().numpy(), A.col, A.row_ptr), shape=(A.n, A.n))
+    G = sp.csr_matrix((g.cpu().numpy(), A.col, A.row_ptr), shape=(n, n))
+    gather = _gather_loss_fn(W, n)
 
-    def loss(vals):
-        (erp, eci, ev), _ = sx.expm(dev(0.5 * vals), 1.0, 1e-12, symmetric=0)
-        E = sp.csr_matrix((ev.cpu().numpy(), eci.cpu().numpy(), erp.cpu().numpy()), shape=(A.n, A.n))
-        return float(E.multiply(Ws).sum())
+    def loss(vals, absolute=False):
+        plan = sx.Plan(dev(0.5 * vals), 1e-12)
+        try:
+            E = plan.compute(1.0)
+            try:
+                erp, eci, ev = E.to_torch()
+            finally:
+                E.free()
+        finally:
+            plan.close()
+        return gather(erp, eci, ev, absolute)
 
     Au = sp.triu(A.to_scipy(), 1).tocoo()
-    rng = np.random.default_rng(3)
-    gmax = abs(G).max()
-    checked = 0
-    for e in rng.choice(Au.nnz, size=8, replace=False):
+    ge = 0.5 * (np.asarray(G[Au.row, Au.col]).ravel() + np.asarray(G[Au.col, Au.row]).ravel())
+    delta = 1e-4 * Au.data
+    noise = 2.0 ** -52 * loss(A.val, absolute=True) / delta
+    ok = np.abs(ge) >= 1e6 * noise
+    print(f"rgg_1e5 adjoint: {ok.sum()} of {len(ge)} edges have a gradient resolvable at 1e-6 by central "
+          f"differences (max |dL/dw| = {np.abs(ge).max():.3e})")
+    assert ok.sum() >= 64
+    pick = np.random.default_rng(3).choice(np.flatnonzero(ok), size=64, replace=False)
+    worst = 0.0
+    for e in pick:
         u, w = int(Au.row[e]), int(Au.col[e])
         puw = A.row_ptr[u] + np.searchsorted(A.col[A.row_ptr[u]:A.row_ptr[u + 1]], w)
         pwu = A.row_ptr[w] + np.searchsorted(A.col[A.row_ptr[w]:A.row_ptr[w + 1]], u)
-        d = 1e-4 * A.val[puw]
+        d = delta[e]
         vp, vm = A.val.copy(), A.val.copy()
         vp[[puw, pwu]] += d
         vm[[puw, pwu]] -= d
         fd = (loss(vp) - loss(vm)) / (2 * d)
-        ad = 0.5 * (G[u, w] + G[w, u])
-        assert abs(ad - fd) <= 1e-6 * max(abs(fd), abs(ad), 1e-3 * gmax), (u, w, ad, fd)
-        checked += 1
-    assert checked == 8
+        rel = abs(ge[e] - fd) / abs(fd)
+        worst = max(worst, rel)
+        print(f"  edge ({u}, {w}): adjoint {ge[e]: .12e}  fd {fd: .12e}  rel {rel:.2e}")
+        assert rel <= 1e-6, (u, w, ge[e], fd)
+    print(f"  worst relative error over 64 edges: {worst:.2e}")
 
 
 def _diag_of(rp, ci, v, n):
