@@ -43,20 +43,28 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kClasses = kProductClasses;
 // Shared-memory budget and block size of each row class; the last class uses global scratch.
-// Blocks have at most 256 threads; the numeric kernel is compiled for SEXPM_NUMERIC_BLOCKS
-// resident 256-thread blocks per SM (its register budget).
+// The symbolic pass uses blocks of at most 256 threads.  The numeric kernel is compiled for
+// 32 resident warps per SM (its register budget: SEXPM_NUMERIC_BLOCKS blocks of 256 threads), and
+// its blocks grow with the class so that every class keeps those 32 warps: a row needing
+// 112 KB (two per SM) runs on 512 threads, a row needing 220 KB or global scratch (one per SM) on
+// 1024.  SEXPM_WIDE_BLOCKS=0 in the environment keeps 256 threads for the wide classes.
 constexpr int kClassBytes[kClasses] = {8 << 10, 24 << 10, 56 << 10, 112 << 10, 220 << 10, INT_MAX};
-constexpr int kClassThreads[kClasses] = {64, 128, 256, 256, 256, 256};
+constexpr int kClassThreads[kClasses] = {64, 128, 256, 256, 256, 256};      // symbolic pass
+constexpr int kNumThreadsWide[kClasses] = {64, 128, 256, 512, 1024, 1024};  // numeric pass
 
 __host__ __device__ constexpr int class_limit(int c) {
   return c == 0 ? (8 << 10) : c == 1 ? (24 << 10) : c == 2 ? (56 << 10) : c == 3 ? (112 << 10)
        : c == 4 ? (220 << 10) : INT_MAX;
 }
 
-__host__ __device__ constexpr int class_warps(int c) { return (c == 0 ? 64 : c == 1 ? 128 : 256) / 32; }
-static_assert(class_warps(0) * 32 == kClassThreads[0] && class_warps(1) * 32 == kClassThreads[1] &&
-                  class_warps(2) * 32 == kClassThreads[2] && class_warps(5) * 32 == kClassThreads[5],
-              "class_warps must match kClassThreads");
+// Warps of the numeric pass's blocks in class c.
+__host__ __device__ constexpr int class_warps(int c, bool wide) {
+  return wide ? (c == 0 ? 2 : c == 1 ? 4 : c == 2 ? 8 : c == 3 ? 16 : 32) : (c == 0 ? 2 : c == 1 ? 4 : 8);
+}
+static_assert(class_warps(0, true) * 32 == kNumThreadsWide[0] && class_warps(3, true) * 32 == kNumThreadsWide[3] &&
+                  class_warps(4, true) * 32 == kNumThreadsWide[4] && class_warps(5, true) * 32 == kNumThreadsWide[5] &&
+                  class_warps(2, false) * 32 == kClassThreads[2] && class_warps(5, false) * 32 == kClassThreads[5],
+              "class_warps must match the block sizes");
 
 // Shared bytes of the numeric pass for a row with W bitmap words, cnt outputs of which cacc
 // are accumulated (the upper part in the symmetric mode), and q accumulators: the
@@ -282,7 +290,8 @@ __global__ void k_analysis(CsrD A, CsrD B, CsrD D, const uint8_t* frozen, int32_
 // mode 0: symbolic need 4 W; mode 1: numeric need 12 W + 8 cnt.
 __global__ void k_classify(int64_t n, const int32_t* sched, const int32_t* words, const int64_t* rp_out,
                            const int32_t* cnt_up, int mode, int ks_bytes, int32_t* lists, int64_t list_stride,
-                           unsigned long long* counts, unsigned long long* maxneed, int64_t r0, int64_t r1) {
+                           unsigned long long* counts, unsigned long long* maxneed, int64_t r0, int64_t r1,
+                           bool wide) {
   __shared__ unsigned int cnt[kClasses];
   __shared__ unsigned long long off[kClasses];
   if (threadIdx.x < kClasses) cnt[threadIdx.x] = 0;
@@ -299,7 +308,7 @@ __global__ void k_classify(int64_t n, const int32_t* sched, const int32_t* words
     if (W > 0) {
       cls = 0;
       for (;;) {
-        need = mode == 0 ? 4 * W : numeric_need(W, full, cacc, class_warps(cls), ks_bytes);
+        need = mode == 0 ? 4 * W : numeric_need(W, full, cacc, class_warps(cls, wide), ks_bytes);
         if (cls == kClasses - 1 || need <= class_limit(cls)) break;
         ++cls;
       }
@@ -401,7 +410,7 @@ __device__ __forceinline__ void build_row_bitmap(const CsrD& A, const WPat& WB, 
 }
 
 // In-place exclusive scan of x[0..W) by the whole block; returns the total to every thread.
-// Each thread scans a contiguous chunk; `red` is a 32-entry shared scratch.
+// Each thread scans a contiguous chunk; `red` is a 33-entry shared scratch.
 __device__ unsigned block_exclusive_scan(unsigned* x, int W, unsigned* red) {
   const int T = blockDim.x, nwarps = T >> 5, lane = lane_id();
   const int ch = (W + T - 1) / T;
@@ -426,7 +435,7 @@ __device__ unsigned block_exclusive_scan(unsigned* x, int W, unsigned* red) {
       if (lane >= o) vi += y;
     }
     if (lane < nwarps) red[lane] = vi - v;
-    if (lane == 31) red[31] = vi;  // block total (nwarps <= 16 < 32)
+    if (lane == 31) red[32] = vi;  // block total (red has 33 entries)
   }
   __syncthreads();
   unsigned run = red[warp_id()] + incl - s;
@@ -435,7 +444,7 @@ __device__ unsigned block_exclusive_scan(unsigned* x, int W, unsigned* red) {
     x[w] = run;
     run += v;
   }
-  const unsigned total = red[31];
+  const unsigned total = red[32];
   __syncthreads();
   return total;
 }
@@ -761,18 +770,18 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
 // Numeric pass.  Layout per row: an accumulator region (the members' accumulators of cacc
 // doubles each; before the accumulation it holds wk[W], the prefix product counts), then
 // bp[W], the bitmap words with their position prefixes.
-template <bool GLOBAL>
-__global__ void __launch_bounds__(256, SEXPM_NUMERIC_BLOCKS) k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, double beta, bool upper,
+template <bool GLOBAL, int NT>
+__global__ void __launch_bounds__(NT, (8 * SEXPM_NUMERIC_BLOCKS * 32) / NT) k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, double beta, bool upper,
                           const uint8_t* frozen, const int32_t* cnt_up, const int32_t* rows,
                           int64_t nrows, const int32_t* base, const int32_t* words, const int64_t* rp_out,
                           int32_t* ci_out, double* v_out, double* row_sq, double* row_diag, unsigned char* gscratch,
                           int64_t gstride, unsigned long long* work_total, unsigned long long* row_ctr,
                           int ks_bytes, int64_t out_base) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned ured[32];
+  __shared__ unsigned ured[33];
   __shared__ double dred[32];
   __shared__ long long s_next;
-  __shared__ double sink[8];  // per-warp target of masked accumulator updates (never read back)
+  __shared__ double sink[NT / 32];  // per-warp target of masked accumulator updates (never read back)
   unsigned char* mem = GLOBAL ? gscratch + (int64_t)blockIdx.x * gstride : smem;
   const int T = blockDim.x;
   const bool hasD = D.n > 0;
@@ -861,6 +870,12 @@ int num_sms() {
   return sms;
 }
 
+// Wide numeric blocks for the wide classes (SEXPM_WIDE_BLOCKS=0 turns them off; read per product).
+bool wide_blocks() {
+  const char* e = std::getenv("SEXPM_WIDE_BLOCKS");
+  return !(e && *e == '0');
+}
+
 // Byte limit of the k split's accumulators: SEXPM_KSPLIT_BYTES from the environment (read on
 // every product, so a process can compare the two accumulation modes), else the default.
 int ksplit_bytes() {
@@ -884,7 +899,9 @@ void set_smem_limits() {
   once_per_device(done, [] {
     const int cap = kClassBytes[kClasses - 2];
     SX_CUDA(cudaFuncSetAttribute(k_symbolic<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    SX_CUDA(cudaFuncSetAttribute(k_numeric<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    SX_CUDA(cudaFuncSetAttribute(k_numeric<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    SX_CUDA(cudaFuncSetAttribute(k_numeric<false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    SX_CUDA(cudaFuncSetAttribute(k_numeric<false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   });
 }
 
@@ -943,6 +960,43 @@ void word_pattern(const CsrD& X, cudaStream_t s, WPatOwned& out, HostScalars& hs
   count_launches(1);
 }
 
+// Arguments of one numeric launch (one size class).
+struct NumericArgs {
+  CsrD A, B, D;
+  WPat WB, WD;
+  double div, beta;
+  bool upper;
+  const uint8_t* frozen;
+  const int32_t* cnt_up;
+  const int32_t* rows;
+  int64_t nrows;
+  const int32_t* base;
+  const int32_t* words;
+  const int64_t* rp_out;
+  int32_t* ci_out;
+  double* v_out;
+  double* row_sq;
+  double* row_diag;
+  unsigned char* gscratch;
+  int64_t gstride;
+  unsigned long long* work_total;
+  unsigned long long* row_ctr;
+  int ks_bytes;
+  int64_t out_base;
+};
+
+// Launches the numeric kernel instance for blocks of NT threads: a persistent grid of the blocks
+// that are resident at once (grid > 0: that many).
+template <bool GLOBAL, int NT>
+void launch_numeric(const NumericArgs& a, int threads, int bytes, cudaStream_t s, int64_t grid = 0) {
+  // (the 64- and 128-thread classes run the 256-thread instance with fewer threads)
+  if (grid == 0) grid = std::min<int64_t>(a.nrows, resident_blocks(k_numeric<GLOBAL, NT>, threads, bytes));
+  k_numeric<GLOBAL, NT><<<(unsigned)grid, threads, bytes, s>>>(
+      a.A, a.B, a.D, a.WB, a.WD, a.div, a.beta, a.upper, a.frozen, a.cnt_up, a.rows, a.nrows, a.base, a.words,
+      a.rp_out, a.ci_out, a.v_out, a.row_sq, a.row_diag, a.gscratch, a.gstride, a.work_total, a.row_ctr,
+      a.ks_bytes, a.out_base);
+}
+
 }  // namespace
 
 void product_symbolic(const CsrD& A, const CsrD& B, const CsrD& D, bool upper, const uint8_t* frozen,
@@ -990,7 +1044,7 @@ void product_symbolic(const CsrD& A, const CsrD& B, const CsrD& D, bool upper, c
     k_sum_i64<<<(unsigned)std::min<int64_t>((n + 255) / 256, sms * 8), 256, 0, s>>>(flops.p, n,
                                                                                  ps.ctr.p + 2 * kClasses + 2);
     k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, sched, ps.words.p, nullptr, nullptr, 0, ps.ks_bytes,
-                                                         ps.lists.p, n, ps.ctr.p, ps.ctr.p + kClasses, 0, n);
+                                                         ps.lists.p, n, ps.ctr.p, ps.ctr.p + kClasses, 0, n, false);
     k_zero_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ps.words.p, n, stats ? stats->sq.p : nullptr,
                                                          stats ? stats->diag.p : nullptr, ps.cnt.p,
                                                          upper ? ps.cnt_up.p : nullptr);
@@ -1046,9 +1100,10 @@ int64_t product_numeric(ProductSym& ps, const CsrD& A, const CsrD& B, const CsrD
   const bool upper = ps.upper;
   SX_CUDA(cudaMemsetAsync(ps.ctr.p, 0, ps.ctr.count * sizeof(unsigned long long), s));
   SX_CUDA(cudaMemsetAsync(ps.row_ctr.p + kClasses, 0, kClasses * sizeof(unsigned long long), s));
+  const bool wide = wide_blocks();
   k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, ps.sched, ps.words.p, ps.row_ptr(),
                                                        upper ? ps.cnt_up.p : nullptr, 1, ps.ks_bytes, ps.lists.p, n,
-                                                       ps.ctr.p, ps.ctr.p + kClasses, r0, r1);
+                                                       ps.ctr.p, ps.ctr.p + kClasses, r0, r1, wide);
   SX_CUDA(cudaGetLastError());
   count_launches(1);
   unsigned long long h[2 * kClasses + 4];
@@ -1059,25 +1114,28 @@ int64_t product_numeric(ProductSym& ps, const CsrD& A, const CsrD& B, const CsrD
   for (int c = 0; c < kClasses; ++c) {
     const int64_t nr = (int64_t)h[c];
     if (!nr) continue;
-    const int threads = kClassThreads[c];
+    const int threads = wide ? kNumThreadsWide[c] : kClassThreads[c];
     const int64_t need = (int64_t)h[kClasses + c];
+    NumericArgs na{A, B, D, WB, WD, div, beta, upper, ps.frozen, upper ? ps.cnt_up.p : nullptr, ps.lists.p + c * n, nr,
+                   ps.base.p, ps.words.p, ps.row_ptr(), ci_out, v_out, stats ? stats->sq.p : nullptr,
+                   stats ? stats->diag.p : nullptr, nullptr, 0, ps.ctr.p + 2 * kClasses + 3,
+                   ps.row_ctr.p + kClasses + c, ps.ks_bytes, out_base};
     if (c < kClasses - 1) {
       const int bytes = (int)((need + 1023) & ~1023ll);
-      const int64_t grid = std::min<int64_t>(nr, resident_blocks(k_numeric<false>, threads, bytes));
-      k_numeric<false><<<(unsigned)grid, threads, bytes, s>>>(
-          A, B, D, WB, WD, div, beta, upper, ps.frozen, upper ? ps.cnt_up.p : nullptr, ps.lists.p + c * n, nr,
-          ps.base.p, ps.words.p, ps.row_ptr(), ci_out, v_out, stats ? stats->sq.p : nullptr,
-          stats ? stats->diag.p : nullptr, nullptr, 0, ps.ctr.p + 2 * kClasses + 3, ps.row_ctr.p + kClasses + c,
-          ps.ks_bytes, out_base);
+      if (threads <= 256) launch_numeric<false, 256>(na, threads, bytes, s);
+      else if (threads == 512) launch_numeric<false, 512>(na, threads, bytes, s);
+      else launch_numeric<false, 1024>(na, threads, bytes, s);
     } else {
       const int64_t stride = (need + 255) & ~255ll;
-      const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
+      // two resident blocks per SM up to 512 threads, one at 1024 (the register budget); the
+      // scratch slices of one wave of blocks then stay within L2 for rows up to ~800 KB
+      const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * (threads >= 1024 ? 1 : 2));
       gs.reset((size_t)(stride * grid), s);
-      k_numeric<true><<<(unsigned)grid, threads, 0, s>>>(
-          A, B, D, WB, WD, div, beta, upper, ps.frozen, upper ? ps.cnt_up.p : nullptr, ps.lists.p + c * n, nr,
-          ps.base.p, ps.words.p, ps.row_ptr(), ci_out, v_out, stats ? stats->sq.p : nullptr,
-          stats ? stats->diag.p : nullptr, gs.p, stride, ps.ctr.p + 2 * kClasses + 3, ps.row_ctr.p + kClasses + c,
-          ps.ks_bytes, out_base);
+      na.gscratch = gs.p;
+      na.gstride = stride;
+      if (threads <= 256) launch_numeric<true, 256>(na, threads, 0, s, grid);
+      else if (threads == 512) launch_numeric<true, 512>(na, threads, 0, s, grid);
+      else launch_numeric<true, 1024>(na, threads, 0, s, grid);
     }
     SX_CUDA(cudaGetLastError());
     count_launches(1);

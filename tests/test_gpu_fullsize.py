@@ -248,7 +248,7 @@ def _diag_of(rp, ci, v, n):
 def test_lap2d_m1500_adjoint_of_trace(sx):
     """The bench workload's adjoint (n = 2.25M): L = trace(P e^{tau H}) through one kept forward
     (sexpm_forward_keep, checkpoints every ceil(sqrt(N)) squarings) and two reverse passes.
-    P = I: dL/dH = (e^{tau H})^T on the pattern of H, every stored entry against the Kronecker
+    P = I: dL/dH = tau (e^{tau H})^T on the pattern of H, every stored entry against the Kronecker
     closed form.  P seeded diagonal (P_ii ~ U[0,1], seed 4): central differences of the GPU
     forward along two diagonal entries and two symmetric off-diagonal pairs, relative error
     <= 1e-6 with no floor."""
@@ -274,7 +274,7 @@ def test_lap2d_m1500_adjoint_of_trace(sx):
     E1 = _sine_basis_expm(m, c.tau)
     rows = np.repeat(np.arange(n), np.diff(H.row_ptr))
     cols = H.col.astype(np.int64)
-    exact = E1[rows // m, cols // m] * E1[rows % m, cols % m]
+    exact = c.tau * E1[rows // m, cols // m] * E1[rows % m, cols % m]   # d trace(e^{tau H})/dH = tau (e^{tau H})^T
     err_I = float(np.abs(g_I - exact).max())
     print(f"adjoint trace: M={st['M']} N={st['N']} |dL/dH - (e^H)^T| max={err_I:.2e} "
           f"peak over forward+reverse={peak / 2**30:.1f} GiB")
