@@ -275,6 +275,10 @@ int sexpm_spgemm(const sexpm_csr_view* A, const sexpm_csr_view* B, const sexpm_c
 int sexpm_filter(const sexpm_csr_view* A, double eps_g, double e_r, int32_t max_iters, void* stream,
                  sexpm_result_t** out, double* t, int32_t* iters, double* b);
 
+/* A^T of a CSR (columns sorted within every row of the result; rows of any length), as used by
+ * the adjoint's reverse pass (Y T^T and T^T Y) and the symmetric part of T^_0. */
+int sexpm_transpose(const sexpm_csr_view* A, void* stream, sexpm_result_t** out);
+
 /* One Algorithm 4.1 reduction pass on the stored values of A (device or host view): the sum of
  * v^2 over the entries with |v| <= t (*sum_dropped) and the number of entries with |v| > t
  * (*kept).  With the threshold sequence t_0 = eps_g, t_{j+1} = eps_g t_j / b_j driven by the caller,

@@ -189,8 +189,8 @@ struct FilterOut {
 // Algorithm 4.1 on the stored values of the row pieces P (together rows 0..n-1, in order), then
 // A~ = A - b_n into `out`.  `extra` is the sum of squares of entries dropped before (by the exact
 // streaming bound, below every threshold the algorithm visits): it joins every pass's sum.
-// Each pass streams the values once and records per-tile kept counts; the compaction after the
-// last pass uses the counts of that pass.
+// Each pass streams the values once and records kept counts per (tile, warp); the compaction
+// after the last pass uses the counts of that pass.
 FilterOut filter_alg41_pieces(const std::vector<Piece>& P, int64_t n, double extra, double eps_g, double e_r,
                               int max_iters, cudaStream_t s, CsrOwned& out, HostScalars& hs) {
   FilterOut r;
@@ -198,7 +198,7 @@ FilterOut filter_alg41_pieces(const std::vector<Piece>& P, int64_t n, double ext
   std::vector<int64_t> tile_base(P.size() + 1, 0);
   int64_t nnz_all = 0;
   for (size_t p = 0; p < P.size(); ++p) {
-    tile_base[p + 1] = tile_base[p] + tiles_of(P[p].nnz);
+    tile_base[p + 1] = tile_base[p] + counts_of(P[p].nnz);
     nnz_all += P[p].nnz;
   }
   const int64_t T = tile_base.back();
@@ -1163,6 +1163,30 @@ int sexpm_spmm(const sexpm_csr_view* A, const double* X, int64_t r, double* Y, v
   SX_API_END
 }
 
+int sexpm_transpose(const sexpm_csr_view* A, void* stream, sexpm_result_t** out) {
+  SX_API_BEGIN
+  if (!A || !out) fail(SEXPM_EINVAL, "null argument");
+  *out = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostScalars hs;
+  CsrOwned a;
+  upload(*A, s, a, hs);
+  sexpm_result* res = new sexpm_result();
+  try {
+    res->s = s;
+    std::memset(&res->st, 0, sizeof(res->st));
+    transpose(a.view(), s, res->E, hs);
+    SX_CUDA(cudaStreamSynchronize(s));
+    res->st.n = res->E.n;
+    res->st.nnz_out = res->E.nnz;
+  } catch (...) {
+    delete res;
+    throw;
+  }
+  *out = res;
+  SX_API_END
+}
+
 int sexpm_filter_pass(const sexpm_csr_view* A, double t, void* stream, double* sum_dropped, int64_t* kept) {
   SX_API_BEGIN
   if (!A || !sum_dropped) fail(SEXPM_EINVAL, "null argument");
@@ -1178,7 +1202,7 @@ int sexpm_filter_pass(const sexpm_csr_view* A, double t, void* stream, double* s
   p.ci = a.ci.p;
   p.v = a.v.p;
   std::vector<Piece> P{p};
-  std::vector<int64_t> base{0, tiles_of(a.nnz)};
+  std::vector<int64_t> base{0, counts_of(a.nnz)};
   DevBuf<int32_t> tc(base[1] ? base[1] : 1, s);
   *sum_dropped = pass_pieces(P, base, t, tc.p, s, hs);
   if (kept) {
@@ -1208,7 +1232,7 @@ int sexpm_filter_apply(const sexpm_csr_view* A, double t, void* stream, sexpm_re
     p.ci = a.ci.p;
     p.v = a.v.p;
     std::vector<Piece> P{p};
-    std::vector<int64_t> base{0, tiles_of(a.nnz)};
+    std::vector<int64_t> base{0, counts_of(a.nnz)};
     DevBuf<int32_t> tc(base[1] ? base[1] : 1, s);
     pass_pieces(P, base, t, tc.p, s, hs);
     res->E.n = a.n;

@@ -7,14 +7,16 @@
 //    prefix counts (rank = position in the row), warps take the entries (i, j) of P_i and
 //    stream row B_j, looking each column up in the bitmap; a warp reduction gives the dot
 //    product.  No atomics; one FMA per matching pair.
-//  * k_sort_rows_block: per-row bitonic sort used by the transpose (rows of up to 4096 entries;
-//    longer rows fall back to an insertion sort).
+//  * k_sort_rows_block / k_sort_long: per-row sorts used by the transpose: a bitonic sort in
+//    shared memory for rows of up to 4096 entries; longer rows sort their 4096-entry chunks the
+//    same way and merge the sorted runs pairwise (merge-path co-ranks) through a scratch array.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <vector>
 
 #include "sexpm_internal.cuh"
 
@@ -151,62 +153,101 @@ __global__ void k_sddmm(CsrD P, CsrD A, CsrD B, double alpha, double beta, int a
   }
 }
 
+// Bitonic sort of entries [p0, p0 + len) (len <= kSortMax) by column, in shared memory, by the
+// whole block.
+__device__ void sort_chunk(int32_t* ci, double* v, int64_t p0, int len, int* sk, double* sv) {
+  int size = 1;
+  while (size < len) size <<= 1;
+  for (int k = threadIdx.x; k < size; k += blockDim.x) {
+    sk[k] = k < len ? ci[p0 + k] : INT_MAX;
+    sv[k] = k < len ? v[p0 + k] : 0.0;
+  }
+  __syncthreads();
+  for (int kk = 2; kk <= size; kk <<= 1) {
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int t = threadIdx.x; t < size; t += blockDim.x) {
+        const int partner = t ^ jj;
+        if (partner > t) {
+          const bool up = (t & kk) == 0;
+          const int a = sk[t], bq = sk[partner];
+          if ((a > bq) == up) {
+            sk[t] = bq;
+            sk[partner] = a;
+            const double x = sv[t];
+            sv[t] = sv[partner];
+            sv[partner] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int k = threadIdx.x; k < len; k += blockDim.x) {
+    ci[p0 + k] = sk[k];
+    v[p0 + k] = sv[k];
+  }
+  __syncthreads();
+}
+
+// Rows of at most kSortMax entries, one block per row (longer rows are left to k_sort_long).
 __global__ void k_sort_rows_block(int64_t n, const int64_t* rp, int32_t* ci, double* v) {
   __shared__ int sk[kSortMax];
   __shared__ double sv[kSortMax];
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     const int64_t p0 = rp[i], p1 = rp[i + 1];
     const int len = (int)(p1 - p0);
-    if (len <= 1) continue;
-    if (len > kSortMax) {
-      if (threadIdx.x == 0) {
-        for (int64_t p = p0 + 1; p < p1; ++p) {
-          const int c = ci[p];
-          const double x = v[p];
-          int64_t q = p - 1;
-          while (q >= p0 && ci[q] > c) {
-            ci[q + 1] = ci[q];
-            v[q + 1] = v[q];
-            --q;
-          }
-          ci[q + 1] = c;
-          v[q + 1] = x;
+    if (len <= 1 || len > kSortMax) continue;
+    sort_chunk(ci, v, p0, len, sk, sv);
+  }
+}
+
+// Rows longer than kSortMax, one block per row (rows[b], scratch slice at off[b] of the row's
+// length): chunks of kSortMax sorted in shared memory, then passes that merge pairs of sorted
+// runs of width w into runs of 2w, alternating between the row and the scratch.  Output
+// position k of a merge takes its element from the co-rank i(k) (the number of elements of the
+// left run among the first k outputs, found by binary search); columns within a row are unique.
+__global__ void k_sort_long(const int64_t* rows, const int64_t* rp, int32_t* ci, double* v, const int64_t* off,
+                            int32_t* sci, double* sv_g) {
+  __shared__ int sk[kSortMax];
+  __shared__ double sv[kSortMax];
+  const int64_t i = rows[blockIdx.x];
+  const int64_t p0 = rp[i];
+  const int64_t len = rp[i + 1] - p0;
+  for (int64_t c0 = 0; c0 < len; c0 += kSortMax)
+    sort_chunk(ci, v, p0 + c0, (int)(len - c0 < kSortMax ? len - c0 : kSortMax), sk, sv);
+  int32_t* srcc = ci + p0;
+  double* srcv = v + p0;
+  int32_t* dstc = sci + off[blockIdx.x];
+  double* dstv = sv_g + off[blockIdx.x];
+  for (int64_t w = kSortMax; w < len; w <<= 1) {
+    for (int64_t a0 = 0; a0 < len; a0 += 2 * w) {
+      const int64_t na = w < len - a0 ? w : len - a0;
+      const int64_t rest = len - a0 - w > 0 ? len - a0 - w : 0;
+      const int64_t nb = w < rest ? w : rest;
+      const int32_t* A = srcc + a0;
+      const int32_t* B = A + na;
+      for (int64_t k = threadIdx.x; k < na + nb; k += blockDim.x) {
+        int64_t lo = k - nb > 0 ? k - nb : 0, hi = k < na ? k : na;
+        while (lo < hi) {  // smallest i with A[i] > B[k - i - 1]
+          const int64_t mid = (lo + hi) >> 1;
+          if (A[mid] <= B[k - mid - 1]) lo = mid + 1; else hi = mid;
         }
-      }
-      __syncthreads();
-      continue;
-    }
-    int size = 1;
-    while (size < len) size <<= 1;
-    for (int k = threadIdx.x; k < size; k += blockDim.x) {
-      sk[k] = k < len ? ci[p0 + k] : INT_MAX;
-      sv[k] = k < len ? v[p0 + k] : 0.0;
-    }
-    __syncthreads();
-    for (int kk = 2; kk <= size; kk <<= 1) {
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (int t = threadIdx.x; t < size; t += blockDim.x) {
-          const int partner = t ^ jj;
-          if (partner > t) {
-            const bool up = (t & kk) == 0;
-            const int a = sk[t], bq = sk[partner];
-            if ((a > bq) == up) {
-              sk[t] = bq;
-              sk[partner] = a;
-              const double x = sv[t];
-              sv[t] = sv[partner];
-              sv[partner] = x;
-            }
-          }
-        }
-        __syncthreads();
+        const int64_t ia = lo, ib = k - lo;
+        const bool take_a = ia < na && (ib >= nb || A[ia] <= B[ib]);
+        const int64_t src = take_a ? a0 + ia : a0 + na + ib;
+        dstc[a0 + k] = srcc[src];
+        dstv[a0 + k] = srcv[src];
       }
     }
-    for (int k = threadIdx.x; k < len; k += blockDim.x) {
-      ci[p0 + k] = sk[k];
-      v[p0 + k] = sv[k];
-    }
     __syncthreads();
+    int32_t* tc = srcc; srcc = dstc; dstc = tc;
+    double* tv = srcv; srcv = dstv; dstv = tv;
+  }
+  if (srcc != ci + p0) {
+    for (int64_t k = threadIdx.x; k < len; k += blockDim.x) {
+      ci[p0 + k] = srcc[k];
+      v[p0 + k] = srcv[k];
+    }
   }
 }
 
@@ -222,12 +263,50 @@ int sms() {
 
 }  // namespace
 
+// Rows longer than kSortMax: their ids and lengths (n_long entries; synchronises s).
+__global__ void k_count_long(int64_t n, const int64_t* rp, unsigned long long* cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && rp[i + 1] - rp[i] > kSortMax) atomicAdd(cnt, 1ull);
+}
+
 void sort_rows(int64_t n, const int64_t* rp, int32_t* ci, double* v, cudaStream_t s) {
   if (n == 0) return;
   const int64_t grid = std::min<int64_t>(n, (int64_t)sms() * 16);
   k_sort_rows_block<<<(unsigned)grid, 256, 0, s>>>(n, rp, ci, v);
   SX_CUDA(cudaGetLastError());
   count_launches(1);
+  // rows longer than kSortMax: found on the host from the row pointers when any exists
+  DevBuf<unsigned long long> cnt(1, s);
+  SX_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
+  k_count_long<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, rp, cnt.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+  unsigned long long h = 0;
+  SX_CUDA(cudaMemcpyAsync(&h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SX_CUDA(cudaStreamSynchronize(s));
+  if (h == 0) return;
+  std::vector<int64_t> rph(n + 1);
+  SX_CUDA(cudaMemcpyAsync(rph.data(), rp, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SX_CUDA(cudaStreamSynchronize(s));
+  std::vector<int64_t> rows, off;
+  int64_t total = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t len = rph[i + 1] - rph[i];
+    if (len > kSortMax) {
+      rows.push_back(i);
+      off.push_back(total);
+      total += len;
+    }
+  }
+  DevBuf<int64_t> drows(rows.size(), s), doff(off.size(), s);
+  DevBuf<int32_t> sci(total, s);
+  DevBuf<double> sv(total, s);
+  SX_CUDA(cudaMemcpyAsync(drows.p, rows.data(), rows.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  SX_CUDA(cudaMemcpyAsync(doff.p, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  k_sort_long<<<(unsigned)rows.size(), 256, 0, s>>>(drows.p, rp, ci, v, doff.p, sci.p, sv.p);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+  SX_CUDA(cudaStreamSynchronize(s));
 }
 
 void sddmm(const CsrD& P, const CsrD& A, const CsrD& B, double alpha, double beta, bool accumulate, double* out,

@@ -3,7 +3,8 @@
 //
 //  * k_pass_flat: one reduction pass, sum of v^2 over |v| <= t, streaming the value array as
 //    16-byte pairs in tiles of kTile entries; it also writes the number of kept entries
-//    (|v| > t) of every tile, so that the compaction after the last pass needs no count pass.
+//    (|v| > t) that each warp saw in each tile, so that the compaction after the last pass needs
+//    no count pass.
 //  * k_compact_flat: A~ = A - b_n, the kept entries of a tile go to the output at the tile's
 //    scanned offset plus their rank inside the tile; the rows that start inside the tile get
 //    their output row pointers from the same ranks.  Neither kernel looks at row boundaries
@@ -32,6 +33,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTile = 2048;          // entries per tile: 256 threads x 4 pairs
 constexpr int kFlatThreads = 256;
+constexpr int kWarpsPerTile = kFlatThreads / 32;  // kept counts per tile (one per warp)
 constexpr int kFlatBlocks = 1024;    // fixed reduction grid of a pass (sums do not depend on timing)
 constexpr int kRowBlocks = 1024;     // fixed grid of the row-wise chunk kernels
 
@@ -79,41 +81,49 @@ __device__ __forceinline__ int2 load_pair_i(const int32_t* c, int64_t e, int64_t
   return r;
 }
 
-// One Algorithm 4.1 pass: part[block] = sum over the block's tiles of v^2 for |v| <= t;
-// tile_cnt[k] = #{|v| > t} in tile k.  Block b takes tiles b, b + grid, ...; each thread
-// loads its four pairs of a tile before using any of them.
+// One Algorithm 4.1 pass: part[block] = sum over the block's tiles of v^2 for |v| <= t, and
+// wcnt[8 k + w] = #{|v| > t} among the entries warp w reads in tile k (its four 64-entry
+// groups).  Block b takes tiles b, b + grid, ...; each thread loads the next tile's four 16-byte
+// pairs before it works on the current ones, and no barrier is taken per tile, so the loads of
+// two tiles are in flight while the block computes (the stream would otherwise be latency-bound).
+template <bool VEC>
+__device__ __forceinline__ void load_tile(const double* v, int64_t nnz, int64_t e0, double2 (&x)[4]) {
+  if (VEC && e0 + kTile <= nnz) {
+    const double2* p = reinterpret_cast<const double2*>(v + e0) + threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = __ldg(p + u * kFlatThreads);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = load_pair<false>(v, e0 + 2 * (u * kFlatThreads + threadIdx.x), nnz);
+  }
+}
+
 template <bool VEC>
 __global__ void __launch_bounds__(kFlatThreads) k_pass_flat(const double* __restrict__ v, int64_t nnz,
-                                                            unsigned long long tb, int32_t* __restrict__ tile_cnt,
+                                                            unsigned long long tb, int32_t* __restrict__ wcnt,
                                                             double* __restrict__ part) {
-  __shared__ int red_c[2][kFlatThreads / 32];
   __shared__ double red_s[kFlatThreads / 32];
   const int64_t tiles = (nnz + kTile - 1) / kTile;
   double s = 0.0;
-  int parity = 0;
-  for (int64_t k = blockIdx.x; k < tiles; k += gridDim.x, parity ^= 1) {
-    const int64_t e0 = k * kTile;
-    double2 x[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) x[u] = load_pair<VEC>(v, e0 + 2 * (u * kFlatThreads + threadIdx.x), nnz);
+  double2 x[4], y[4];
+  int64_t k = blockIdx.x;
+  if (k < tiles) load_tile<VEC>(v, nnz, k * kTile, x);
+  for (; k < tiles; k += gridDim.x) {
+    const int64_t kn = k + gridDim.x;
+    if (kn < tiles) load_tile<VEC>(v, nnz, kn * kTile, y);
     int c = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (above(x[u].x, tb)) ++c; else s = fma(x[u].x, x[u].x, s);
-      if (above(x[u].y, tb)) ++c; else s = fma(x[u].y, x[u].y, s);
+      const bool a0 = above(x[u].x, tb), a1 = above(x[u].y, tb);
+      c += __popc(__ballot_sync(FULL, a0)) + __popc(__ballot_sync(FULL, a1));
+      if (!a0) s = fma(x[u].x, x[u].x, s);
+      if (!a1) s = fma(x[u].y, x[u].y, s);
     }
-    c = warp_sum(c);
-    if (lane_id() == 0) red_c[parity][warp_id()] = c;
-    __syncthreads();  // double-buffered counts: one barrier per tile
-    if (threadIdx.x == 0) {
-      int t = 0;
+    if (lane_id() == 0) wcnt[k * kWarpsPerTile + warp_id()] = c;
 #pragma unroll
-      for (int w = 0; w < kFlatThreads / 32; ++w) t += red_c[parity][w];
-      tile_cnt[k] = t;
-    }
+    for (int u = 0; u < 4; ++u) x[u] = y[u];
   }
   s = warp_sum(s);
-  __syncthreads();
   if (lane_id() == 0) red_s[warp_id()] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -163,9 +173,10 @@ __device__ int64_t warp_lower_bound(const int64_t* rp, int64_t n, int64_t x) {
 }
 
 // Compaction of one piece by tiles (one block per tile).  Kept entries (|v| > t) of tile k go
-// to out_ci/out_v at tile_off[k] + their rank among the tile's kept entries; rows of the piece
-// whose first entry lies in tile k (for the last tile also the rows that start at nnz) get
-// out_rp[i] = tile_off[k] + the number of kept entries of the tile before that entry.
+// to out_ci/out_v at tile_off[8 k] (the scan of the pass's per-warp counts at the tile's first
+// warp) + their rank among the tile's kept entries; rows of the piece whose first entry lies in
+// tile k (for the last tile also the rows that start at nnz) get out_rp[i] = that offset + the
+// number of kept entries of the tile before that entry.
 template <bool VEC>
 __global__ void __launch_bounds__(kFlatThreads) k_compact_flat(const int64_t* __restrict__ rp, int64_t nrows,
                                                                const int32_t* __restrict__ ci,
@@ -190,11 +201,22 @@ __global__ void __launch_bounds__(kFlatThreads) k_compact_flat(const int64_t* __
   double2 x[4];
   int2 c[4];
   unsigned b0[4], b1[4];
+  if (VEC && e0 + kTile <= nnz) {
+    // a full tile: eight unconditional 16- and 8-byte loads in flight per thread
+    const double2* pv = reinterpret_cast<const double2*>(v + e0) + threadIdx.x;
+    const int2* pc = reinterpret_cast<const int2*>(ci + e0) + threadIdx.x;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int64_t e = e0 + 2 * (u * kFlatThreads + threadIdx.x);
-    x[u] = load_pair<VEC>(v, e, nnz);
-    c[u] = load_pair_i<VEC>(ci, e, nnz);
+    for (int u = 0; u < 4; ++u) {
+      x[u] = __ldg(pv + u * kFlatThreads);
+      c[u] = __ldg(pc + u * kFlatThreads);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t e = e0 + 2 * (u * kFlatThreads + threadIdx.x);
+      x[u] = load_pair<false>(v, e, nnz);
+      c[u] = load_pair_i<false>(ci, e, nnz);
+    }
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -233,7 +255,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_compact_flat(const int64_t* __
     wpre[2 * lane + 1] = wi - p1;
   }
   __syncthreads();
-  const int64_t base = tile_off[k];
+  const int64_t base = tile_off[k * kWarpsPerTile];
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -434,6 +456,7 @@ double norm2_I_plus_rows(const CsrD& A, int64_t r0, int64_t r1, cudaStream_t s, 
 // ---------------------------------------------------------------- host side
 
 int64_t tiles_of(int64_t nnz) { return (nnz + kTile - 1) / kTile; }
+int64_t counts_of(int64_t nnz) { return tiles_of(nnz) * kWarpsPerTile; }
 
 double pass_pieces(const std::vector<Piece>& P, const std::vector<int64_t>& tile_base, double t, int32_t* tile_cnt,
                    cudaStream_t s, HostScalars& hs) {
@@ -496,8 +519,8 @@ void compact_pieces(const std::vector<Piece>& P, const std::vector<int64_t>& til
     count_launches(1);
   }
   // out.rp[n] = total kept (the scan's last entry)
-  const int64_t total_tiles = tile_base.empty() ? 0 : tile_base.back();
-  SX_CUDA(cudaMemcpyAsync(out.rp.p + n, tile_off + total_tiles, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  const int64_t total_counts = tile_base.empty() ? 0 : tile_base.back();
+  SX_CUDA(cudaMemcpyAsync(out.rp.p + n, tile_off + total_counts, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
 }
 
 double drop_rows(int64_t r0, int64_t r1, const int64_t* rp, int64_t base, const int32_t* ci, double* v, bool sym,

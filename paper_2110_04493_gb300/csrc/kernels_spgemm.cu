@@ -44,13 +44,15 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kClasses = kProductClasses;
 // Shared-memory budget and block size of each row class; the last class uses global scratch.
 // The symbolic pass uses blocks of at most 256 threads.  The numeric kernel is compiled for
-// 32 resident warps per SM (its register budget: SEXPM_NUMERIC_BLOCKS blocks of 256 threads), and
-// its blocks grow with the class so that every class keeps those 32 warps: a row needing
-// 112 KB (two per SM) runs on 512 threads, a row needing 220 KB or global scratch (one per SM) on
-// 1024.  SEXPM_WIDE_BLOCKS=0 in the environment keeps 256 threads for the wide classes.
+// 32 resident warps per SM (its register budget: SEXPM_NUMERIC_BLOCKS blocks of 256 threads).
+// Rows of the global-scratch class (accumulators in L2) run on blocks of 1024 threads, one per
+// SM, which keeps those 32 warps there (measured on the 3-D 64^3 grid: its last squaring 118 s ->
+// 82 s); the 112 KB and 220 KB classes measured 5-18% slower on 512 or 1024 threads than on 256
+// (more column groups, each searching every B row) and stay at 256.  SEXPM_WIDE_BLOCKS=0 in the
+// environment keeps 256 threads for the global class too.
 constexpr int kClassBytes[kClasses] = {8 << 10, 24 << 10, 56 << 10, 112 << 10, 220 << 10, INT_MAX};
 constexpr int kClassThreads[kClasses] = {64, 128, 256, 256, 256, 256};      // symbolic pass
-constexpr int kNumThreadsWide[kClasses] = {64, 128, 256, 512, 1024, 1024};  // numeric pass
+constexpr int kNumThreadsWide[kClasses] = {64, 128, 256, 256, 256, 1024};  // numeric pass
 
 __host__ __device__ constexpr int class_limit(int c) {
   return c == 0 ? (8 << 10) : c == 1 ? (24 << 10) : c == 2 ? (56 << 10) : c == 3 ? (112 << 10)
@@ -59,7 +61,7 @@ __host__ __device__ constexpr int class_limit(int c) {
 
 // Warps of the numeric pass's blocks in class c.
 __host__ __device__ constexpr int class_warps(int c, bool wide) {
-  return wide ? (c == 0 ? 2 : c == 1 ? 4 : c == 2 ? 8 : c == 3 ? 16 : 32) : (c == 0 ? 2 : c == 1 ? 4 : 8);
+  return wide ? (c == 0 ? 2 : c == 1 ? 4 : c <= 4 ? 8 : 32) : (c == 0 ? 2 : c == 1 ? 4 : 8);
 }
 static_assert(class_warps(0, true) * 32 == kNumThreadsWide[0] && class_warps(3, true) * 32 == kNumThreadsWide[3] &&
                   class_warps(4, true) * 32 == kNumThreadsWide[4] && class_warps(5, true) * 32 == kNumThreadsWide[5] &&
@@ -566,37 +568,82 @@ __device__ __forceinline__ void load_quad(const CsrD& B, int lane, Quad& q) {
   }
 }
 
-// acc[rank(c_t)] += a v_t for the NC chunks of quad q; an entry with a column below c_lo (the
-// upper mode's entries below the diagonal) is sent to the warp's sink slot instead.  The
-// columns of a quad are distinct (one row of B; repeated last entries aside), so every rank
-// and accumulator load is issued before the first store and the chunks' DFMAs overlap.  The
-// code is branch-free; every chunk has a lane inside the segment, so no DFMA is issued for a
-// chunk without work.
-template <int NC>
-__device__ __forceinline__ void accumulate_chunks(double* acc, double* sink, const uint2* bp, int b, int c_lo,
-                                                  const Quad& q) {
-  double* ad[NC];
-  double x[NC];
-#pragma unroll
-  for (int t = 0; t < NC; ++t) {
-    const int c = q.c[t];
-    double* const at = acc + rank_of(bp, c - b);
-    ad[t] = c >= c_lo ? at : sink;
-  }
-#pragma unroll
-  for (int t = 0; t < NC; ++t) x[t] = *ad[t];
-#pragma unroll
-  for (int t = 0; t < NC; ++t) x[t] = fma(q.a, q.v[t], x[t]);
-#pragma unroll
-  for (int t = 0; t < NC; ++t) *ad[t] = x[t];
+// Shared-memory accesses through 32-bit shared-window addresses (the accumulators and the
+// bitmap words of the shared-memory classes).
+__device__ __forceinline__ uint2 lds_u2(uint32_t a) {
+  uint2 r;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(a));
+  return r;
+}
+__device__ __forceinline__ double lds_f64(uint32_t a) {
+  double r;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(r) : "r"(a));
+  return r;
+}
+__device__ __forceinline__ void sts_f64(uint32_t a, double x) {
+  asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(x) : "memory");
 }
 
-__device__ __forceinline__ void accumulate_quad(double* acc, double* sink, const uint2* bp, int b, int c_lo,
-                                                const Quad& q) {
-  if (q.len > 96) accumulate_chunks<4>(acc, sink, bp, b, c_lo, q);
-  else if (q.len > 64) accumulate_chunks<3>(acc, sink, bp, b, c_lo, q);
-  else if (q.len > 32) accumulate_chunks<2>(acc, sink, bp, b, c_lo, q);
-  else accumulate_chunks<1>(acc, sink, bp, b, c_lo, q);
+// Addresses of the accumulation: generic pointers (global-scratch rows) and, for rows held in
+// shared memory, the same arrays as 32-bit shared-window addresses.
+struct AccPtrs {
+  double* acc;
+  double* sink;
+  const uint2* bp;
+  uint32_t acc_s, sink_s, bp_s;
+  int c_lo;  // with MASK, entries below this column go to the sink
+};
+
+// acc[rank(c_t)] += a v_t for the NC chunks of quad q; with MASK an entry with a column below
+// P.c_lo (the upper mode's entries below the diagonal) is sent to the warp's sink slot instead
+// (only rows whose k's are not split into column groups need it: short rows of B are masked
+// rather than searched).
+// The columns of a quad are distinct (one row of B; repeated last entries aside), so every rank
+// and accumulator load is issued before the first store and the chunks' DFMAs overlap.  The
+// code is branch-free; every chunk has a lane inside the segment, so no DFMA is issued for a
+// chunk without work.  SH: the accumulators and bitmap are in shared memory (32-bit addresses).
+template <int NC, bool MASK, bool SH>
+__device__ __forceinline__ void accumulate_chunks(const AccPtrs& P, int b, const Quad& q) {
+  double x[NC];
+  if (SH) {
+    uint32_t ad[NC];
+#pragma unroll
+    for (int t = 0; t < NC; ++t) {
+      const int c = q.c[t];
+      const unsigned rel = (unsigned)(c - b);
+      const uint2 e = lds_u2(P.bp_s + (rel >> 5) * 8u);
+      const uint32_t at = P.acc_s + (e.y + __popc((e.x << (~rel & 31u)) << 1)) * 8u;
+      ad[t] = (!MASK || c >= P.c_lo) ? at : P.sink_s;
+    }
+#pragma unroll
+    for (int t = 0; t < NC; ++t) x[t] = lds_f64(ad[t]);
+#pragma unroll
+    for (int t = 0; t < NC; ++t) x[t] = fma(q.a, q.v[t], x[t]);
+#pragma unroll
+    for (int t = 0; t < NC; ++t) sts_f64(ad[t], x[t]);
+  } else {
+    double* ad[NC];
+#pragma unroll
+    for (int t = 0; t < NC; ++t) {
+      const int c = q.c[t];
+      double* const at = P.acc + rank_of(P.bp, c - b);
+      ad[t] = (!MASK || c >= P.c_lo) ? at : P.sink;
+    }
+#pragma unroll
+    for (int t = 0; t < NC; ++t) x[t] = *ad[t];
+#pragma unroll
+    for (int t = 0; t < NC; ++t) x[t] = fma(q.a, q.v[t], x[t]);
+#pragma unroll
+    for (int t = 0; t < NC; ++t) *ad[t] = x[t];
+  }
+}
+
+template <bool MASK, bool SH>
+__device__ __forceinline__ void accumulate_quad_m(const AccPtrs& P, int b, const Quad& q) {
+  if (q.len > 96) accumulate_chunks<4, MASK, SH>(P, b, q);
+  else if (q.len > 64) accumulate_chunks<3, MASK, SH>(P, b, q);
+  else if (q.len > 32) accumulate_chunks<2, MASK, SH>(P, b, q);
+  else accumulate_chunks<1, MASK, SH>(P, b, q);
 }
 
 // One stage of the accumulation pipeline: fix the quad after `cur` (the next 128 entries of
@@ -604,9 +651,9 @@ __device__ __forceinline__ void accumulate_quad(double* acc, double* sink, const
 // lanes' s, len, a and the mask `live` of segments not yet started), start its loads, then
 // accumulate `cur`.  Returns false when `cur` was the batch's last quad.  Between two
 // segments the warp synchronises: rows B_k and B_k' may share columns.
-__device__ __forceinline__ bool pipe_stage(const CsrD& B, double* acc, double* sink, const uint2* bp, int b,
-                                           int lane, int c_lo, int64_t s, int len, double a, unsigned& live,
-                                           const Quad& cur, Quad& nxt) {
+template <bool MASK, bool SH>
+__device__ __forceinline__ bool pipe_stage(const CsrD& B, const AccPtrs& P, int b, int lane, int64_t s, int len,
+                                           double a, unsigned& live, const Quad& cur, Quad& nxt) {
   bool more = true, fresh = false;
   if (cur.len > 128) {
     nxt.s = cur.s + 128;
@@ -623,7 +670,7 @@ __device__ __forceinline__ bool pipe_stage(const CsrD& B, double* acc, double* s
     more = false;
   }
   if (more) load_quad(B, lane, nxt);
-  accumulate_quad(acc, sink, bp, b, c_lo, cur);
+  accumulate_quad_m<MASK, SH>(P, b, cur);
   if (fresh) __syncwarp();
   return more;
 }
@@ -631,6 +678,7 @@ __device__ __forceinline__ bool pipe_stage(const CsrD& B, double* acc, double* s
 // Numeric pass, one row: prefixes, accumulation, fused scaling and beta D, and the ordered
 // write.  The accumulator region first holds wk (products per word); bp holds the row's
 // bitmap words with their position prefixes.
+template <bool SH>
 __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double div, double beta, bool upper, bool fz,
                             int i, int W, int b, int64_t o0, int cnt, int lo_pos, double* acc, unsigned* wk,
                             uint2* bp, double* sink, int32_t* ci_out, double* v_out, double* row_sq,
@@ -675,6 +723,20 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
       const int c_lo = upper ? max(b + 32 * wa, i) : b + 32 * wa;
       const int c_hi = b + 32 * wb - 1;
       double* const accw = acc + q * cacc;
+      // short rows of B are masked entry by entry (upper mode, one column group)
+      const bool mask_row = upper && groups == 1;
+      AccPtrs P;
+      P.c_lo = c_lo;
+      P.acc = accw;
+      P.sink = sink;
+      P.bp = bp;
+      if (SH) {
+        // 32-bit shared addresses; acc is indexed by full-row position and may start before the
+        // region (modular arithmetic brings every accessed position back inside)
+        P.acc_s = (uint32_t)__cvta_generic_to_shared(acc + lo_pos) - 8u * (uint32_t)lo_pos + 8u * (uint32_t)(q * cacc);
+        P.sink_s = (uint32_t)__cvta_generic_to_shared(sink);
+        P.bp_s = (uint32_t)__cvta_generic_to_shared(bp);
+      }
       const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
       for (int64_t kb = a0 + q; kb < a1; kb += 32 * members) {
         const int64_t p = kb + lane * members;
@@ -715,8 +777,14 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
           qa.a = __shfl_sync(FULL, a, j);
           load_quad(B, lane, qa);
         }
-        while (pipe_stage(B, accw, sink, bp, b, lane, c_lo, s, len, a, live, qa, qb) &&
-               pipe_stage(B, accw, sink, bp, b, lane, c_lo, s, len, a, live, qb, qa)) {
+        if (mask_row) {
+          while (pipe_stage<true, SH>(B, P, b, lane, s, len, a, live, qa, qb) &&
+                 pipe_stage<true, SH>(B, P, b, lane, s, len, a, live, qb, qa)) {
+          }
+        } else {
+          while (pipe_stage<false, SH>(B, P, b, lane, s, len, a, live, qa, qb) &&
+                 pipe_stage<false, SH>(B, P, b, lane, s, len, a, live, qb, qa)) {
+          }
         }
         __syncwarp();
       }
@@ -807,7 +875,7 @@ __global__ void __launch_bounds__(NT, (8 * SEXPM_NUMERIC_BLOCKS * 32) / NT) k_nu
     const bool fz = frozen && frozen[i];
     build_row_bitmap<2>(A, WB, WD, hasD, i, b >> 5, reinterpret_cast<uint32_t*>(bp), wk, upper, fz);
     __syncthreads();
-    numeric_row(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, cnt - cacc, acc, wk, bp, &sink[threadIdx.x >> 5],
+    numeric_row<!GLOBAL>(A, B, D, div, beta, upper, fz, i, W, b, o0, cnt, cnt - cacc, acc, wk, bp, &sink[threadIdx.x >> 5],
                 ci_out, v_out, row_sq, row_diag, ured, dred, work_total, ks_bytes);
     if (threadIdx.x == 0) s_next = nxt;
     __syncthreads();

@@ -242,15 +242,17 @@ struct Piece {
   const double* v = nullptr;
 };
 
-// Tiles of the flat filter kernels covering nnz entries.
+// Tiles of the flat filter kernels covering nnz entries, and their kept counts (one per warp
+// of a tile).
 int64_t tiles_of(int64_t nnz);
+int64_t counts_of(int64_t nnz);
 // One Algorithm 4.1 pass over all pieces: returns sum_{|v| <= t} v^2 and writes the kept
-// count (|v| > t) of every tile (piece p's tiles start at tile_cnt + tile_base[p]).
-// Synchronises s.
+// counts (|v| > t) of every tile and warp (piece p's counts start at tile_cnt + tile_base[p],
+// tile_base in units of counts_of).  Synchronises s.
 double pass_pieces(const std::vector<Piece>& P, const std::vector<int64_t>& tile_base, double t, int32_t* tile_cnt,
                    cudaStream_t s, HostScalars& hs);
 // Compaction of the entries |v| > t of all pieces into out (rows 0..n-1; out.rp/ci/v allocated);
-// tile_off = exclusive scan of the tile counts of the last pass (total at tile_off[total tiles]).
+// tile_off = exclusive scan of the counts of the last pass (total at tile_off[total counts]).
 void compact_pieces(const std::vector<Piece>& P, const std::vector<int64_t>& tile_base, double t,
                     const int64_t* tile_off, int64_t n, CsrOwned& out, cudaStream_t s);
 // Exact streaming step of a row chunk [r0, r1) of an unfiltered product (row i at

@@ -99,6 +99,7 @@ def load() -> ctypes.CDLL:
     L.sexpm_compute_batched.argtypes = [vp, P(ctypes.c_double), P(vp)]
     L.sexpm_adjoint.argtypes = [vp, ctypes.c_double, P(CsrView), ctypes.c_int32, P(vp), P(vp)]
     L.sexpm_forward_keep.argtypes = [vp, ctypes.c_double, ctypes.c_int32, P(vp), P(vp)]
+    L.sexpm_transpose.argtypes = [P(CsrView), vp, P(vp)]
     L.sexpm_result_spmm.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
     L.sexpm_propagate.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
     L.sexpm_spmm.argtypes = [P(CsrView), vp, ctypes.c_int64, vp, vp]
@@ -491,6 +492,19 @@ def spmm(A, X):
     Y = torch.empty_like(X2)
     _check(load().sexpm_spmm(ctypes.byref(a), X2.data_ptr(), X2.shape[1], Y.data_ptr(), _stream_ptr()))
     return Y.reshape(-1) if vec else Y
+
+
+def transpose(A, device="cuda"):
+    """A^T (sexpm_transpose) as (row_ptr, col, val) torch tensors."""
+    keep: List[Any] = []
+    a = _make_view(A, keep)
+    r = ctypes.c_void_p()
+    _check(load().sexpm_transpose(ctypes.byref(a), _stream_ptr(), ctypes.byref(r)))
+    res = Result(r.value)
+    try:
+        return res.to_torch(device)
+    finally:
+        res.free()
 
 
 def filter_pass(A, t: float) -> Tuple[float, int]:

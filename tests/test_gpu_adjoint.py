@@ -145,3 +145,26 @@ def test_autograd_edge_parameterisation(sx):
     ref = beta * (np.asarray(Go[Au.row, Au.col]).ravel() + np.asarray(Go[Au.col, Au.row]).ravel())
     got = w.grad.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-9 * max(np.abs(ref).max(), 1e-300)
+
+
+@pytest.mark.parametrize("long_len", [5000, 30000])
+def test_transpose_with_long_rows_matches_scipy(sx, long_len):
+    """The transpose behind the reverse pass: rows of the result longer than the 4096 entries a
+    block sorts in shared memory (a column of 5000 or 30000 entries) are merged from sorted runs;
+    the result equals scipy's transpose entry for entry."""
+    rng = np.random.default_rng(long_len)
+    n = 40000
+    A = sp.random(n, n, density=4 / n, random_state=np.random.RandomState(1), format="lil")
+    rows = rng.choice(n, size=long_len, replace=False)
+    A[rows, 5] = rng.uniform(-1, 1, long_len)[:, None]
+    A[rows[:long_len // 2], 777] = rng.uniform(-1, 1, long_len // 2)[:, None]
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    rp, ci, v = sx.transpose(torch_csr(CSR.from_scipy(A)))
+    G = to_scipy(rp, ci, v, n)
+    R = sp.csr_matrix(A.T)
+    R.sort_indices()
+    assert np.array_equal(G.indptr, R.indptr)
+    assert np.array_equal(G.indices, R.indices)
+    assert np.array_equal(G.data, R.data)
+    assert np.diff(G.indptr).max() >= long_len
