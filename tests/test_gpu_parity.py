@@ -334,3 +334,25 @@ def test_spgemm_reaches_every_size_class(sx):
     assert rows[5] >= 1, rows          # global-memory accumulators
     assert rows[0] > 0, rows
     assert 39000 < sum(rows) <= 40000, rows  # every non-empty product row is in exactly one class
+
+
+# ------------------------------------------------------------------ structural vibration (Eq. 2.1-2.2)
+
+def test_expm_structural_vibration_theta(sx):
+    """H = Theta dt for a damped 12 x 12 spring lattice (Rayleigh C = 0.02 M + 0.01 K): non-normal and
+    non-symmetric (a = 1/||H||_F, every product entry formed), at the parity bar against the oracle."""
+    from workloads import theta_lattice
+    H = theta_lattice(12, 2, seed=4, dt=0.7, alpha=0.02, beta=0.01)
+    res, st, so = _check_method(sx, H, 1.0, 1e-12)
+    assert not st["normal"] and not st["symmetric"]
+
+
+def test_expm_theta_chain_closed_form(sx):
+    """The undamped chain's propagator against its closed form (cos/sin of (K/m)^(1/2) dt)."""
+    from tests.test_oracle_pins import _chain_exact, _chain_theta
+    m, k, m0, dt = 40, 1.3, 0.7, 0.9
+    H = _chain_theta(m, k, m0, dt)
+    (rp, ci, v), st = sx.expm(torch_csr(_csr(H)), 1.0, 1e-14)
+    G = to_scipy(rp, ci, v, 2 * m).toarray()
+    X = _chain_exact(m, k, m0, dt)
+    assert np.abs(G - X).max() <= 1e-12 * np.abs(X).sum(axis=0).max()

@@ -401,3 +401,65 @@ def test_alg41_thresholds_are_bounded_below_so_it_streams_exactly():
         assert b2 == pytest.approx(b, rel=1e-12, abs=1e-300)
         assert np.array_equal(np.abs(v) > t, np.abs(v) > t2)
     assert streamed_some > 30
+
+
+# ------------------------------------------------------------------ structural vibration (Eq. 2.1-2.2)
+
+def _chain_theta(m, k, m0, dt):
+    """Theta dt for a chain of m equal masses m0 joined by equal springs k, with springs to fixed
+    walls at both ends (K = k trid(-1, 2, -1)), no damping."""
+    import scipy.sparse as sp
+    from workloads import theta_matrix
+    K = sp.diags([-k * np.ones(m - 1), 2 * k * np.ones(m), -k * np.ones(m - 1)], [-1, 0, 1], format="csr")
+    T = theta_matrix(K, m0 * np.ones(m))
+    return sp.csr_matrix((T.val * dt, T.col, T.row_ptr), shape=(2 * m, 2 * m))
+
+
+def _chain_exact(m, k, m0, dt):
+    """e^{Theta dt} = [[cos(W dt), W^-1 sin(W dt)], [-W sin(W dt), cos(W dt)]], W = (K/m0)^(1/2), from the
+    sine eigenbasis of trid(-1, 2, -1): eigenvalues 4 sin^2(j pi / (2(m+1))), j = 1..m."""
+    j = np.arange(1, m + 1)
+    w = np.sqrt(4 * k / m0) * np.sin(j * np.pi / (2 * (m + 1)))
+    V = np.sqrt(2.0 / (m + 1)) * np.sin(np.outer(j, j) * np.pi / (m + 1))
+    f = lambda d: (V * d) @ V.T
+    c, s = np.cos(w * dt), np.sin(w * dt)
+    return np.block([[f(c), f(s / w)], [f(-w * s), f(c)]])
+
+
+def test_oracle_theta_chain_matches_closed_form():
+    """The undamped chain's propagator (Eq. 2.2) against its closed form: the method as the oracle
+    restates it reaches the exact e^{Theta dt} to ~1e-13 of its norm (non-normal H, a = 1/||H||_F)."""
+    m, k, m0, dt = 30, 1.3, 0.7, 0.9
+    H = _chain_theta(m, k, m0, dt)
+    E, st = O.expm(H, 1.0, 1e-14)
+    assert not st.normal
+    X = _chain_exact(m, k, m0, dt)
+    assert np.abs(E.toarray() - X).max() <= 1e-12 * np.abs(X).sum(axis=0).max()
+
+
+def test_oracle_theta_undamped_lattice_conserves_energy():
+    """Without damping the flow of Eq. (2.1) keeps the energy (a^T K a + v^T M v)/2: for random
+    states U, the oracle's e^H U has the same energy to ~1e-12 (relative)."""
+    import scipy.sparse as sp
+    from workloads import spring_lattice, theta_matrix
+    K, masses = spring_lattice(8, 2, seed=3)
+    T = theta_matrix(K, masses)
+    H = sp.csr_matrix((T.val * 0.8, T.col, T.row_ptr), shape=(T.n, T.n))
+    E, st = O.expm(H, 1.0, 1e-14)
+    G = sp.block_diag([K, sp.diags(masses)]).tocsr()
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        U = rng.standard_normal(T.n)
+        Y = E @ U
+        e0, e1 = U @ (G @ U), Y @ (G @ Y)
+        assert abs(e1 - e0) <= 1e-12 * e0
+
+
+def test_oracle_theta_damped_lattice_matches_pade():
+    """A damped lattice (Rayleigh C = 0.02 M + 0.01 K) against scipy's Pade expm."""
+    import scipy.linalg as sla
+    from workloads import theta_lattice
+    H = theta_lattice(6, 2, seed=4, dt=0.7, alpha=0.02, beta=0.01).to_scipy()
+    E, st = O.expm(H, 1.0, 1e-14)
+    X = sla.expm(H.toarray())
+    assert np.abs(E.toarray() - X).max() <= 1e-12 * np.abs(X).sum(axis=0).max()

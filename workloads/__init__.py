@@ -19,5 +19,8 @@ from .generators import (  # noqa: F401
     random_csr,
     rgg_adjacency,
     sparse_loss_weights,
+    spring_lattice,
+    theta_lattice,
+    theta_matrix,
     toeplitz_trid,
 )

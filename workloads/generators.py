@@ -163,6 +163,59 @@ def paper_table1_matrices() -> List[np.ndarray]:
     return [H1, H2, H3, H4, H5]
 
 
+def spring_lattice(m: int, dim: int, seed: int, klo: float = 0.5, khi: float = 1.5, mlo: float = 0.5,
+                   mhi: float = 2.0) -> Tuple[sp.csr_matrix, np.ndarray]:
+    """Stiffness K and lumped masses of an m^dim lattice of point masses joined to their grid
+    neighbours by springs, with springs to fixed walls at the boundary (so K is SPD): spring
+    stiffness ~ U[klo, khi], masses ~ U[mlo, mhi] (seeded).  Node (x, y, z) has index
+    x + m y + m^2 z."""
+    rng = np.random.default_rng(seed)
+    n = m ** dim
+    idx = np.arange(n).reshape((m,) * dim)
+    rows, cols, ks = [], [], []
+    diag = np.zeros(n)
+    for ax in range(dim):
+        # springs between neighbours along this axis, and to the walls at both ends
+        lo = np.take(idx, range(0, m - 1), axis=ax).ravel()
+        hi = np.take(idx, range(1, m), axis=ax).ravel()
+        k = rng.uniform(klo, khi, size=lo.size)
+        rows += [lo, hi]
+        cols += [hi, lo]
+        ks += [-k, -k]
+        np.add.at(diag, lo, k)
+        np.add.at(diag, hi, k)
+        for end in (0, m - 1):
+            w = np.take(idx, [end], axis=ax).ravel()
+            diag[w] += rng.uniform(klo, khi, size=w.size)
+    rows.append(np.arange(n))
+    cols.append(np.arange(n))
+    ks.append(diag)
+    K = sp.csr_matrix((np.concatenate(ks), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    K.sum_duplicates()
+    K.sort_indices()
+    masses = rng.uniform(mlo, mhi, size=n)
+    return K, masses
+
+
+def theta_matrix(K: sp.csr_matrix, masses: np.ndarray, alpha: float = 0.0, beta: float = 0.0) -> CSR:
+    """Theta = [[0, I], [-M^-1 K, -M^-1 C]] of U' = Theta U, U = (displacements, velocities), for a
+    lumped (diagonal) mass matrix M and Rayleigh damping C = alpha M + beta K (Eq. 2.1)."""
+    n = K.shape[0]
+    Minv = sp.diags(1.0 / masses)
+    I = sp.identity(n, format="csr")
+    MK = Minv @ K
+    MC = alpha * I + beta * MK
+    T = sp.bmat([[None, I], [-MK, -MC]], format="csr")
+    return CSR.from_scipy(T)
+
+
+def theta_lattice(m: int, dim: int, seed: int, dt: float, alpha: float = 0.0, beta: float = 0.0) -> CSR:
+    """H = Theta dt (Eq. 2.2) for a seeded spring lattice (see spring_lattice)."""
+    K, masses = spring_lattice(m, dim, seed)
+    T = theta_matrix(K, masses, alpha, beta)
+    return CSR(T.n, T.row_ptr, T.col, T.val * dt)
+
+
 @dataclasses.dataclass
 class Config:
     """A named workload: matrix builder, tau, tolerance and a description."""
@@ -189,6 +242,9 @@ CONFIGS: Dict[str, Config] = {
                           "2-D 5-point Dirichlet Laplacian, 1500x1500 grid (n=2.25M), h=1/1501, tau=1e-6, eps=1e-12"),
     "rgg_1e5": Config("rgg_1e5", lambda: rgg_adjacency(100_000, seed=3), 0.5, 1e-12,
                       "random geometric graph, n=1e5, mean degree 10, weights U[0.5,1.5], H = 0.5*A, eps=1e-12"),
+    "theta_m300": Config("theta_m300", lambda: theta_lattice(300, 2, seed=6, dt=1.0, alpha=1e-3, beta=1e-3), 1.0,
+                         1e-12, "structural vibration: Theta of a 300x300 spring lattice (n = 180,000), springs "
+                                "U[0.5,1.5], masses U[0.5,2], Rayleigh damping 1e-3 M + 1e-3 K, dt = 1, eps = 1e-12"),
     "toeplitz_trid_n1e4": Config("toeplitz_trid_n1e4", lambda: toeplitz_trid(10_000, 1.0, -2.0, 1.0), 1.0, 1e-16,
                                  "trid(1,-2,1), n=10000, eps=1e-16 (paper Sec. 5.2, Tables 2-3)"),
     "toeplitz_heat_n1e4": Config("toeplitz_heat_n1e4", lambda: toeplitz_trid(10_000, -1.0 / 10_001, 2.0 / 10_001, -1.0 / 10_001),
