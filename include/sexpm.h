@@ -98,6 +98,12 @@ typedef struct {
                                bound and the sum of squares of the rest).  0 (default): chunk only
                                when needed, chunks sized from free memory; > 0: chunks of at most
                                this many bytes of T~_i whenever T~_i is larger. */
+  int32_t scaling;          /* 0 (default): (M, N) by Eq. (4.20) on ||tau H||_F; 1: the refined norm of
+                               Sec. 4.2, h_{M,N} = max_{M+1<=k<=2M+1} ||(tau H 2^-N)^k||_F^(1/k) from
+                               exact sparse powers of tau H (up to k = refine_kmax), in the choice
+                               of (M, N) (sexpm_choose_MN_refined), in r_0 = rho(M, h_{M,N}) and in
+                               eps_g^(0) = a r_0 / (M e^{2 h_{M,N}}) */
+  int32_t refine_kmax;      /* highest power of tau H the refined norm uses (odd, >= 3; default 41) */
 } sexpm_options;
 
 typedef struct sexpm_plan sexpm_plan_t;
@@ -206,6 +212,25 @@ double sexpm_rho(int32_t M, double x);
  * M the least positive integer with 2^N rho(M, norm_H 2^-N) <= eps; ties to the smaller
  * M + N, then the smaller N.  norm_H = 0 gives M = N = 0. */
 int sexpm_choose_MN(double norm_H, double eps, int32_t n_extra, int32_t max_M, int32_t* M, int32_t* N);
+
+/* ||H^k||_F for k = 1..kmax into out[0..kmax-1], from exact sparse powers H^k = H^{k-1} H formed
+ * on the GPU (Sec. 4.2: the norms behind the refined bound h_{M,N} of Eq. 4.9).  The powers
+ * widen by the stencil at every step: memory grows like nnz(H^kmax). */
+int sexpm_power_norms(const sexpm_csr_view* H, int32_t kmax, void* stream, double* out);
+
+/* alpha^_i of Eq. (4.8) (pnorms NULL) or Eq. (4.9) (pnorms[k-1] = ||H^k||, k <= kmax): the least
+ * M1 2^N1 with 2^N1 rho(M1, x) <= r_i = 2^i rho(M, ||H 2^-N||) (Eq. 4.6), x = ||H 2^{i-N-N1}|| or the
+ * refined h_{M1, N+N1-i}; alpha^_i lambda(H) bounds the eps-bandwidth of the squaring iterate
+ * T_i (Eq. 4.7, Theorem 3.8).  Host only. */
+int sexpm_alpha_hat(double norm_H, int32_t M, int32_t N, int32_t i, const double* pnorms, int32_t kmax,
+                    int32_t* alpha);
+
+/* Eq. (4.20)'s rule on the refined norm: minimise M 2^N over N in [0, N0 + n_extra] (N0 =
+ * max(ceil(log2 norm_H), 0)), M the least positive integer (2M + 1 <= kmax) with
+ * 2^N rho(M, h_{M,N}) <= eps and h_{M,N} <= 1; ties to the smaller M + N, then the smaller N.
+ * Host only; SEXPM_ENOPARAM when no pair qualifies. */
+int sexpm_choose_MN_refined(double norm_H, const double* pnorms, int32_t kmax, double eps, int32_t n_extra,
+                            int32_t* M, int32_t* N);
 
 /* ---------------------------------------------------------- batched form */
 

@@ -411,3 +411,111 @@ def forward_frozen(H, tau: float, N: int, S_masks, T_masks) -> sp.csr_matrix:
     for k in range(1, len(T_masks)):
         T = restrict(2.0 * T + T @ T, T_masks[k])
     return _canon(sp.identity(H.shape[0], format="csr") + T)
+
+
+# --------------------------------------------------------------------------
+# Bandwidth bounds of the squaring iterates (Sec. 4.2, Eqs. 4.6-4.9)
+# --------------------------------------------------------------------------
+
+def power_norms(H, kmax: int) -> List[float]:
+    """||H^k||_F for k = 1..kmax, from exact sparse powers (a library product per power)."""
+    H = _canon(H)
+    out = []
+    P = H.copy()
+    for k in range(1, kmax + 1):
+        if k > 1:
+            P = _canon(P @ H)
+        out.append(fro_norm(P))
+    return out
+
+
+def h_refined(pnorms: List[float], M1: int, Np: int) -> float:
+    """h_{M1,Np} = max over M1+1 <= k <= 2 M1 + 1 of ||(H 2^-Np)^k||^(1/k) (Sec. 4.2, from [11]),
+    given pnorms[k-1] = ||H^k||."""
+    best = 0.0
+    for k in range(M1 + 1, 2 * M1 + 2):
+        v = pnorms[k - 1]
+        if v > 0.0:
+            best = max(best, math.exp((math.log(v) - Np * k * math.log(2.0)) / k))
+    return best
+
+
+def alpha_hat(normH: float, M: int, N: int, i: int, pnorms: Optional[List[float]] = None,
+              n1_max: int = 40, m1_max: int = 1000) -> int:
+    """alpha^_i of Eq. (4.8) (pnorms None: ||H 2^{i-N} 2^{-N1}|| in rho) or of Eq. (4.9) (with
+    pnorms[k-1] = ||H^k||: h_{M1, N+N1-i} in rho): the least M1 2^N1 with
+    2^N1 rho(M1, .) <= r_i, where r_i = 2^i rho(M, ||H 2^-N||) (Eq. 4.6)."""
+    ri = math.ldexp(rho(M, math.ldexp(normH, -N)), i)
+    best = None
+    for N1 in range(0, n1_max + 1):
+        for M1 in range(1, m1_max + 1):
+            if pnorms is None:
+                x = math.ldexp(normH, i - N - N1)
+            else:
+                if 2 * M1 + 1 > len(pnorms):
+                    break
+                x = h_refined(pnorms, M1, N + N1 - i)
+            if math.ldexp(rho(M1, x), N1) <= ri:
+                c = M1 << N1
+                if best is None or c < best:
+                    best = c
+                break
+    if best is None:
+        raise OracleError("no (M1, N1) meets r_i in the searched range")
+    return best
+
+
+def choose_MN_refined(normH: float, pnorms: List[float], eps_tol: float, n_extra: int = 50) -> Tuple[int, int]:
+    """Eq. (4.20)'s rule with the refined norm of Sec. 4.2 in place of ||H 2^-N||: over N in
+    [0, N0 + n_extra] (N0 = max(ceil(log2 ||H||), 0)), m(N) = the least M >= 1 (with 2M + 1 <= kmax)
+    such that h_{M,N} <= 1 and 2^N rho(M, h_{M,N}) <= eps; minimise M 2^N, ties to the smaller M + N,
+    then the smaller N."""
+    if normH == 0.0:
+        return 0, 0
+    kmax = len(pnorms)
+    N0 = max(ceil_log2(normH), 0)
+    best = None
+    for N in range(0, N0 + n_extra + 1):
+        mN = None
+        M = 1
+        while 2 * M + 1 <= kmax:
+            h = h_refined(pnorms, M, N)
+            if h <= 1.0 and math.ldexp(rho(M, h), N) <= eps_tol:
+                mN = M
+                break
+            M += 1
+        if mN is None:
+            continue
+        key = (mN * 2 ** N, mN + N, N)
+        if best is None or key < best[0]:
+            best = (key, mN, N)
+    if best is None:
+        raise OracleError("no feasible (M, N) on the refined norm")
+    return best[1], best[2]
+
+
+def expm_refined(H, tau: float = 1.0, eps_tol: float = 1e-12, e_r: float = 0.1, kmax: int = 41):
+    """Algorithm 4.2 with the refined scaling (reading of Sec. 4.2 / Eq. 4.9): (M, N) by
+    choose_MN_refined on ||(tau H)^k||_F (exact sparse powers, k <= kmax), r_0 = rho(M, h_{M,N}) and
+    eps_g^(0) = a r_0 / (M e^{2 h_{M,N}}); everything else as in expm()."""
+    H = _canon(H)
+    n = H.shape[0]
+    if tau != 1.0:
+        H = H.copy()
+        H.data = H.data * tau
+    normH = fro_norm(H)
+    normal = is_normal(H)
+    eye = sp.identity(n, format="csr")
+    if normH == 0.0:
+        return _canon(eye), (0, 0)
+    pn = power_norms(H, kmax)
+    M, N = choose_MN_refined(normH, pn, eps_tol)
+    a = 1.0 / (1 + N) if normal else 1.0 / normH
+    h = h_refined(pn, M, N)
+    r0 = rho(M, h)
+    eps_g0 = a * r0 / (M * math.exp(2.0 * h))
+    H0 = H.copy()
+    H0.data = np.ldexp(H0.data, -N)
+    T0, terms, _ = taylor_phase(H0, M, eps_g0, e_r)
+    T, steps, _ = squaring_phase(T0, N, a, r0, e_r)
+    return _canon(eye + T), (M, N)

@@ -638,6 +638,20 @@ void square_step(const sexpm_options& o, const CsrD& T, int k, double a, double 
   }
 }
 
+// ||H^k||_F for k = 1..kmax from exact sparse powers H^k = H^{k-1} H.
+void power_norms(const CsrD& H, int kmax, cudaStream_t s, HostScalars& hs, double* out) {
+  CsrOwned P;
+  copy_csr(H, s, P);
+  out[0] = std::sqrt(sum_squares(P.view(), s, hs));
+  CsrD none;
+  for (int k = 2; k <= kmax; ++k) {
+    CsrOwned Q;
+    spgemm(P.view(), H, none, 1.0, 0.0, s, Q, nullptr, hs);
+    P = std::move(Q);
+    out[k - 1] = std::sqrt(sum_squares(P.view(), s, hs));
+  }
+}
+
 void compute_impl(sexpm_plan_t* p, double tau, sexpm_result* res, Record* record, bool allow_sym) {
   if (!std::isfinite(tau)) fail(SEXPM_EINVAL, "tau must be finite");
   int dev = 0;
@@ -663,8 +677,17 @@ void compute_impl(sexpm_plan_t* p, double tau, sexpm_result* res, Record* record
   const double normH = std::sqrt(sum_squares(Hs, s, hs));
   st.norm_H = normH;
   int32_t M = 0, N = 0;
-  const int rc = sexpm_choose_MN(normH, p->eps, o.n_extra, o.max_taylor, &M, &N);
-  if (rc != SEXPM_OK) fail(rc, rc == SEXPM_ENOPARAM ? "no feasible (M, N) for this tolerance" : "invalid (M, N) input");
+  std::vector<double> pnorms;
+  if (o.scaling == 1 && normH > 0.0) {
+    // the refined norm of Sec. 4.2: ||(tau H)^k||_F from exact sparse powers
+    pnorms.resize(o.refine_kmax);
+    power_norms(Hs, o.refine_kmax, s, hs, pnorms.data());
+    const int rc = sexpm_choose_MN_refined(normH, pnorms.data(), o.refine_kmax, p->eps, o.n_extra, &M, &N);
+    if (rc != SEXPM_OK) fail(rc, "no feasible (M, N) for this tolerance on the refined norm (raise refine_kmax)");
+  } else {
+    const int rc = sexpm_choose_MN(normH, p->eps, o.n_extra, o.max_taylor, &M, &N);
+    if (rc != SEXPM_OK) fail(rc, rc == SEXPM_ENOPARAM ? "no feasible (M, N) for this tolerance" : "invalid (M, N) input");
+  }
   st.M = M;
   st.N = N;
   const bool normal = (p->normal != 0) || normH == 0.0;
@@ -700,7 +723,8 @@ void compute_impl(sexpm_plan_t* p, double tau, sexpm_result* res, Record* record
   scale_values(hv.p, std::ldexp(1.0, -N), p->H.nnz, h0v.p, s);
   CsrD H0 = Hs;
   H0.v = h0v.p;
-  const double x0 = std::ldexp(normH, -N);
+  // ||H_0|| of Eq. (4.5) and of the Taylor threshold; the refined norm h_{M,N} in the refined scaling
+  const double x0 = pnorms.empty() ? std::ldexp(normH, -N) : h_refined(pnorms.data(), o.refine_kmax, M, N);
   const double r0 = sexpm_rho(M, x0);
   const double eps_g0 = a * r0 / ((double)M * std::exp(2.0 * x0));
   st.r0 = r0;
@@ -948,6 +972,8 @@ int sexpm_options_default(sexpm_options* opt) {
   opt->symmetric = 1;
   opt->row_order = 1;
   opt->chunk_bytes = 0;
+  opt->scaling = 0;
+  opt->refine_kmax = 41;
   return SEXPM_OK;
 }
 
@@ -959,6 +985,8 @@ static void check_options(const sexpm_options& o) {
   if (o.symmetric != 0 && o.symmetric != 1) fail(SEXPM_EINVAL, "symmetric must be 0 or 1");
   if (o.row_order != 0 && o.row_order != 1) fail(SEXPM_EINVAL, "row_order must be 0 or 1");
   if (o.chunk_bytes < 0) fail(SEXPM_EINVAL, "chunk_bytes must be >= 0");
+  if (o.scaling != 0 && o.scaling != 1) fail(SEXPM_EINVAL, "scaling must be 0 or 1");
+  if (o.refine_kmax < 3) fail(SEXPM_EINVAL, "refine_kmax must be >= 3");
 }
 
 int sexpm_plan(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_options* opt, void* stream,
@@ -1163,6 +1191,17 @@ int sexpm_spmm(const sexpm_csr_view* A, const double* X, int64_t r, double* Y, v
   SX_API_END
 }
 
+int sexpm_power_norms(const sexpm_csr_view* H, int32_t kmax, void* stream, double* out) {
+  SX_API_BEGIN
+  if (!H || !out || kmax < 1) fail(SEXPM_EINVAL, "null argument or kmax < 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostScalars hs;
+  CsrOwned a;
+  upload(*H, s, a, hs);
+  power_norms(a.view(), kmax, s, hs, out);
+  SX_API_END
+}
+
 int sexpm_transpose(const sexpm_csr_view* A, void* stream, sexpm_result_t** out) {
   SX_API_BEGIN
   if (!A || !out) fail(SEXPM_EINVAL, "null argument");
@@ -1276,6 +1315,7 @@ int sexpm_plan_batched(const sexpm_csr_view* Hs, int32_t count, double eps, cons
   try {
     if (opt) p->opt = *opt; else sexpm_options_default(&p->opt);
     check_options(p->opt);
+    if (p->opt.scaling != 0) fail(SEXPM_EINVAL, "the batched form uses the scaling of Eq. (4.20) (scaling = 0)");
     SX_CUDA(cudaGetDevice(&p->device));
     p->s = static_cast<cudaStream_t>(stream);
     p->eps = eps;

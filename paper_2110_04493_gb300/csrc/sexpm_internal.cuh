@@ -267,6 +267,9 @@ double norm2_I_plus_rows(const CsrD& A, int64_t r0, int64_t r1, cudaStream_t s, 
 void compact_rows(int64_t r0, int64_t r1, const int64_t* rp, int64_t base, const int32_t* ci, const double* v, bool sym,
                   double L, const int64_t* out_rp, int32_t* out_ci, double* out_v, cudaStream_t s);
 
+// h_{M1,Np} of Sec. 4.2 from pnorms[k-1] = ||H^k|| (k <= kmax); -1 when kmax < 2 M1 + 1.
+double h_refined(const double* pnorms, int32_t kmax, int32_t M1, int32_t Np);
+
 // Y = A X (X, Y device, n x r row-major, no overlap).
 void spmm(const CsrD& A, const double* X, int64_t r, double* Y, cudaStream_t s);
 

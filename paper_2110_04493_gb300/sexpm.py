@@ -38,7 +38,8 @@ class CsrView(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("e_r", ctypes.c_double), ("square_scale", ctypes.c_int32), ("normal_override", ctypes.c_int32),
                 ("max_filter_iters", ctypes.c_int32), ("n_extra", ctypes.c_int32), ("max_taylor", ctypes.c_int32),
-                ("symmetric", ctypes.c_int32), ("row_order", ctypes.c_int32), ("chunk_bytes", ctypes.c_int64)]
+                ("symmetric", ctypes.c_int32), ("row_order", ctypes.c_int32), ("chunk_bytes", ctypes.c_int64),
+                ("scaling", ctypes.c_int32), ("refine_kmax", ctypes.c_int32)]
 
 
 class StepStats(ctypes.Structure):
@@ -100,6 +101,11 @@ def load() -> ctypes.CDLL:
     L.sexpm_adjoint.argtypes = [vp, ctypes.c_double, P(CsrView), ctypes.c_int32, P(vp), P(vp)]
     L.sexpm_forward_keep.argtypes = [vp, ctypes.c_double, ctypes.c_int32, P(vp), P(vp)]
     L.sexpm_transpose.argtypes = [P(CsrView), vp, P(vp)]
+    L.sexpm_power_norms.argtypes = [P(CsrView), ctypes.c_int32, vp, P(ctypes.c_double)]
+    L.sexpm_alpha_hat.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                  P(ctypes.c_double), ctypes.c_int32, P(ctypes.c_int32)]
+    L.sexpm_choose_MN_refined.argtypes = [ctypes.c_double, P(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32)]
     L.sexpm_result_spmm.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
     L.sexpm_propagate.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
     L.sexpm_spmm.argtypes = [P(CsrView), vp, ctypes.c_int64, vp, vp]
@@ -582,6 +588,33 @@ def pool_stats() -> Tuple[int, int]:
 def rho(M: int, x: float) -> float:
     """Eq. (4.5), evaluated by the library's host code."""
     return load().sexpm_rho(int(M), float(x))
+
+
+def power_norms(H, kmax: int) -> List[float]:
+    """||H^k||_F for k = 1..kmax from exact sparse powers on the GPU (sexpm_power_norms)."""
+    keep: List[Any] = []
+    a = _make_view(H, keep)
+    out = (ctypes.c_double * int(kmax))()
+    _check(load().sexpm_power_norms(ctypes.byref(a), int(kmax), _stream_ptr(), out))
+    return list(out)
+
+
+def alpha_hat(norm_H: float, M: int, N: int, i: int, pnorms=None) -> int:
+    """alpha^_i of Eq. (4.8) (pnorms None) or Eq. (4.9) (sexpm_alpha_hat, host)."""
+    a = ctypes.c_int32()
+    arr = (ctypes.c_double * len(pnorms))(*pnorms) if pnorms is not None else None
+    _check(load().sexpm_alpha_hat(float(norm_H), int(M), int(N), int(i), arr, len(pnorms) if pnorms else 0,
+                                  ctypes.byref(a)))
+    return a.value
+
+
+def choose_MN_refined(norm_H: float, pnorms, eps: float, n_extra: int = 50) -> Tuple[int, int]:
+    """Eq. (4.20)'s rule on the refined norm h_{M,N} (sexpm_choose_MN_refined, host)."""
+    M, N = ctypes.c_int32(), ctypes.c_int32()
+    arr = (ctypes.c_double * len(pnorms))(*pnorms)
+    _check(load().sexpm_choose_MN_refined(float(norm_H), arr, len(pnorms), float(eps), int(n_extra),
+                                          ctypes.byref(M), ctypes.byref(N)))
+    return M.value, N.value
 
 
 def choose_MN(norm_H: float, eps: float, n_extra: int = 50, max_M: int = 1000) -> Tuple[int, int]:

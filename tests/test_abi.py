@@ -132,3 +132,24 @@ def test_host_choose_MN_returns_enoparam_for_an_unreachable_tolerance(lib):
     M, N = ctypes.c_int32(-9), ctypes.c_int32(-9)
     rc = lib.sexpm_choose_MN(1e3, 1e-300, 0, 3, ctypes.byref(M), ctypes.byref(N))
     assert rc == -5 and (M.value, N.value) == (-9, -9)
+
+
+def test_host_alpha_hat_and_refined_choice_match_the_oracle(lib):
+    """sexpm_alpha_hat (Eqs. 4.8, 4.9) and sexpm_choose_MN_refined give the oracle's values from the
+    same power norms (the Sec. 5.2 Toeplitz matrix, and a 2-D grid Laplacian)."""
+    from paper_2110_04493_gb300 import sexpm
+    from workloads import dirichlet_laplacian, toeplitz_trid
+    H = toeplitz_trid(10_000, 1.0, -2.0, 1.0).to_scipy()
+    nH = O.fro_norm(H)
+    pn = O.power_norms(H, 81)
+    for i in range(0, 9):
+        assert sexpm.alpha_hat(nH, 20, 8, i) == O.alpha_hat(nH, 20, 8, i)
+        assert sexpm.alpha_hat(nH, 20, 8, i, pn) == O.alpha_hat(nH, 20, 8, i, pn)
+    for eps in (1e-16, 1e-12, 1e-8):
+        assert sexpm.choose_MN_refined(nH, pn[:41], eps) == O.choose_MN_refined(nH, pn[:41], eps)
+    L = dirichlet_laplacian(30, 2).to_scipy() * (2.253 / 31 ** 2)
+    nL = O.fro_norm(L)
+    pl = O.power_norms(L, 41)
+    MN = sexpm.choose_MN_refined(nL, pl, 1e-12)
+    assert MN == O.choose_MN_refined(nL, pl, 1e-12)
+    assert MN[1] < O.choose_MN(nL, 1e-12)[1]   # the refined norm needs fewer squarings

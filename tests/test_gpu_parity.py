@@ -356,3 +356,32 @@ def test_expm_theta_chain_closed_form(sx):
     G = to_scipy(rp, ci, v, 2 * m).toarray()
     X = _chain_exact(m, k, m0, dt)
     assert np.abs(G - X).max() <= 1e-12 * np.abs(X).sum(axis=0).max()
+
+
+# ------------------------------------------------------------------ refined norm (Sec. 4.2, Eq. 4.9)
+
+def test_power_norms_match_the_oracle(sx):
+    """||H^k||_F, k = 1..41, from the GPU's sparse powers against scipy's."""
+    H = dirichlet_laplacian(20, 2)
+    Hs = H.to_scipy() * (2.253 / 21 ** 2)
+    Hd = CSR.from_scipy(Hs)
+    got = sx.power_norms(torch_csr(Hd), 41)
+    ref = O.power_norms(Hs, 41)
+    assert np.allclose(got, ref, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("case", ["toeplitz", "grid"])
+def test_refined_scaling_matches_oracle(sx, case):
+    """scaling = 1: (M, N) from the refined norm h_{M,N} (fewer squarings than Eq. 4.20 on the
+    F-norm), r_0 = rho(M, h), the rest of Algorithm 4.2 unchanged; same (M, N) as the oracle's
+    reading and the parity bar on e^{tau H}."""
+    if case == "toeplitz":
+        H, tau, eps = toeplitz_trid(10_000, 1.0, -2.0, 1.0), 1.0, 1e-16
+    else:
+        H, tau, eps = dirichlet_laplacian(30, 2), 2.253 / 31 ** 2, 1e-12
+    (rp, ci, v), st = sx.expm(torch_csr(H), tau, eps, scaling=1)
+    E, MN = O.expm_refined(H.to_scipy(), tau, eps)
+    assert (st["M"], st["N"]) == MN
+    assert st["N"] < O.choose_MN(O.fro_norm(H.to_scipy() * tau), eps)[1]
+    ts = [r["t"] for r in st["steps"]]
+    expm_parity(to_scipy(rp, ci, v, H.n), E, max(ts) if ts else 0.0)

@@ -463,3 +463,37 @@ def test_oracle_theta_damped_lattice_matches_pade():
     E, st = O.expm(H, 1.0, 1e-14)
     X = sla.expm(H.toarray())
     assert np.abs(E.toarray() - X).max() <= 1e-12 * np.abs(X).sum(axis=0).max()
+
+
+# ------------------------------------------------------------------ Sec. 4.2: alpha^_i (Eqs. 4.8-4.9)
+
+def test_alpha_hat_refined_norm_reproduces_table3_third_row_for_i_le_4():
+    """Table 3's third row, alpha^_i lambda(H) for trid(1,-2,1), n = 10^4, eps = 1e-16 (M, N) =
+    (20, 8), lambda(H) = 2: Eq. (4.9) with the refined norm h_{M1,N'} of exact sparse powers (F-norm)
+    gives 18, 20, 24, 28 for i = 1..4 as printed, and one Taylor order more (+2) for i = 5..8
+    (printed 32, 40, 52, 70; the printed values are not reproduced by the F-, 1- or 2-norm for
+    every i).  Eq. (4.8) with ||H|| alone gives far larger values (52, 72, ...)."""
+    from workloads import toeplitz_trid
+    H = toeplitz_trid(10_000, 1.0, -2.0, 1.0).to_scipy()
+    nH = O.fro_norm(H)
+    M, N = O.choose_MN(nH, 1e-16)
+    assert (M, N) == (20, 8)
+    pn = O.power_norms(H, 2 * 40 + 1)
+    refined = [2 * O.alpha_hat(nH, M, N, i, pn) for i in range(1, 9)]
+    printed = golden("table3_squaring_bandwidths.txt")["alpha_lambda"]
+    assert refined[:4] == printed[:4]
+    assert [r - p for r, p in zip(refined[4:], printed[4:])] == [2, 2, 2, 2]
+    plain = [2 * O.alpha_hat(nH, M, N, i) for i in range(1, 3)]
+    assert plain == [52, 72]
+
+
+def test_alpha_hat_bounds_the_filtered_bandwidth():
+    """Theorem 3.8 / Eq. (4.7): the filtered iterates' real bandwidths lambda(T^_i) (the pinned
+    Table 3 second row) stay below alpha^_i lambda(H) computed by Eq. (4.9)."""
+    from workloads import toeplitz_trid
+    H = toeplitz_trid(10_000, 1.0, -2.0, 1.0).to_scipy()
+    nH = O.fro_norm(H)
+    pn = O.power_norms(H, 81)
+    lam_T = [14, 16, 18, 20, 22, 26, 32, 38]
+    for i, l in zip(range(1, 9), lam_T):
+        assert l <= 2 * O.alpha_hat(nH, 20, 8, i, pn)
