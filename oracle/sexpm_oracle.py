@@ -35,6 +35,9 @@ Readings of the paper taken here (the paper is silent or ambiguous on them):
   ("absolute") is available as an option.  The relative reading is the
   default because it reproduces Table 3.
 * e^H = I + T^_N, the diagonal inserted where T^_N has no stored entry.
+* Complex H (the method is stated for C^{n x n}): |v| is the modulus, the sums of
+  Algorithm 4.1 and the Frobenius norms add |v|^2 = re^2 + im^2, and the normality
+  test uses the conjugate transpose.  Real input takes exactly the real path.
 """
 from __future__ import annotations
 
@@ -56,11 +59,18 @@ class OracleError(RuntimeError):
 # Norms and scalar bounds
 # --------------------------------------------------------------------------
 
+def abs2(v) -> np.ndarray:
+    """|v|^2 of real or complex values (re^2 + im^2 for complex)."""
+    v = np.asarray(v)
+    if np.iscomplexobj(v):
+        return v.real.astype(np.float64) ** 2 + v.imag.astype(np.float64) ** 2
+    return np.asarray(v, dtype=np.float64) ** 2
+
+
 def fro_norm(A) -> float:
     """Frobenius norm sqrt(sum |a_ij|^2) over the stored entries (Sec. 5)."""
     v = A.data if sp.issparse(A) else np.asarray(A).ravel()
-    return math.sqrt(math.fsum((np.asarray(v, dtype=np.float64) ** 2).tolist())) if len(v) < 200000 \
-        else float(np.sqrt(np.sum(np.square(np.asarray(v, dtype=np.float64)))))
+    return math.sqrt(math.fsum(abs2(v).tolist())) if len(v) < 200000 else float(np.sqrt(np.sum(abs2(v))))
 
 
 def rho(M: int, x: float) -> float:
@@ -87,6 +97,23 @@ def rho(M: int, x: float) -> float:
         if k > 10000:
             break
     return total
+
+
+def scale_pow2(v, e: int) -> np.ndarray:
+    """v 2^e, exact (real or complex values)."""
+    v = np.asarray(v)
+    if np.iscomplexobj(v):
+        return np.ldexp(v.real, e) + 1j * np.ldexp(v.imag, e)
+    return np.ldexp(v, e)
+
+
+def div_real(v, d) -> np.ndarray:
+    """v / d for a real d, each part divided once (for complex v numpy's complex division would
+    round differently)."""
+    v = np.asarray(v)
+    if np.iscomplexobj(v):
+        return v.real / d + 1j * (v.imag / d)
+    return v / d
 
 
 def ceil_log2(x: float) -> int:
@@ -119,8 +146,9 @@ def choose_MN(normH: float, eps_tol: float, n_extra: int = 50, m_cap: int = 1000
 
 
 def is_normal(H: sp.csr_matrix) -> bool:
-    """Normality test (reading of Algorithm 4.2 step 2, see module docstring)."""
-    Ht = H.T.tocsr()
+    """Normality test (reading of Algorithm 4.2 step 2, see module docstring); H^T is the
+    conjugate transpose for complex H (normal: H H^* = H^* H)."""
+    Ht = H.conj().T.tocsr()
     if (H != Ht).nnz == 0 or (H + Ht).count_nonzero() == 0:
         return True
     C = (H @ Ht) - (Ht @ H)
@@ -147,7 +175,9 @@ def alg41_threshold(vals: np.ndarray, eps_g: float, e_r: float, max_iter: int = 
     Returns (eps_f, iterations, b): the entries with |v| > eps_f are kept, the
     rest (whose F-norm is b <= eps_g (1 + e_r)) are dropped.
     """
-    stash = np.abs(np.asarray(vals, dtype=np.float64))
+    vals = np.asarray(vals)
+    mag = np.asarray(np.abs(vals), dtype=np.float64)  # |v|: the modulus for complex values
+    sq = abs2(vals)                                   # |v|^2 (re^2 + im^2 for complex)
     m = 1.0
     b = math.inf  # the first pass always runs (reading of the b_0 sentinel)
     n = 0
@@ -156,8 +186,9 @@ def alg41_threshold(vals: np.ndarray, eps_g: float, e_r: float, max_iter: int = 
         if n >= max_iter:
             raise OracleError("Algorithm 4.1 did not converge")
         eps_f = eps_g / m
-        stash = stash[stash <= eps_f]          # b_n(p) = 0 for |b_n| > eps_f
-        b = float(np.sqrt(np.sum(stash * stash)))
+        keep = mag <= eps_f                    # b_n(p) = 0 for |b_n| > eps_f
+        mag, sq = mag[keep], sq[keep]
+        b = float(np.sqrt(np.sum(sq)))
         m = b / eps_f
         n += 1
     return eps_f, n, b
@@ -242,7 +273,7 @@ def taylor_phase(H0: sp.csr_matrix, M: int, eps_g0: float, e_r: float, max_iter:
     for i in range(2, M + 1):
         prev = S
         St = _canon(S @ H0)
-        St.data = St.data / i          # S~_i = S^_{i-1} H_0 / i
+        St.data = div_real(St.data, i)  # S~_i = S^_{i-1} H_0 / i
         S, info = filter_csr(St, eps_g0, e_r, max_iter)
         terms.append(TaylorTerm(i, St.nnz, S.nnz, info.t, info.iters, product_count(prev, H0)))
         if S.nnz == 0:
@@ -314,7 +345,7 @@ def expm(H, tau: float = 1.0, eps_tol: float = 1e-12, e_r: float = 0.1, square_s
         stats.nnz_out = E.nnz
         return (E, stats, None) if keep else (E, stats)
     H0 = H.copy()
-    H0.data = np.ldexp(H0.data, -N)            # H_0 = H 2^-N (exact)
+    H0.data = scale_pow2(H0.data, -N)          # H_0 = H 2^-N (exact)
     T0, terms, kept_terms = taylor_phase(H0, M, eps_g0, e_r, max_iter, keep_terms=keep)
     stats.taylor = terms
     stats.nnz_T0 = T0.nnz
@@ -515,7 +546,7 @@ def expm_refined(H, tau: float = 1.0, eps_tol: float = 1e-12, e_r: float = 0.1, 
     r0 = rho(M, h)
     eps_g0 = a * r0 / (M * math.exp(2.0 * h))
     H0 = H.copy()
-    H0.data = np.ldexp(H0.data, -N)
+    H0.data = scale_pow2(H0.data, -N)
     T0, terms, _ = taylor_phase(H0, M, eps_g0, e_r)
     T, steps, _ = squaring_phase(T0, N, a, r0, e_r)
     return _canon(eye + T), (M, N)
