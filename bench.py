@@ -189,44 +189,67 @@ def run_reference(args):
 
 
 def measure_batched(sexpm, torch, steps: int = 2):
-    """Batched form (256 independent 2-D Laplacians, one block-diagonal run) against the plain
-    per-matrix loop on the same GPU; inputs resident on the device for both."""
+    """Batched form (256 independent 2-D Laplacians, one block-diagonal run): the captured squaring
+    step (one CUDA graph launch per squaring, sizes decided on the device), the same run with
+    host-driven launches, and the plain per-matrix loop, on the same GPU with inputs resident on
+    the device."""
     from workloads import BATCH_EPS, laplacian_batch
     items = laplacian_batch()
     devs = [(torch.from_numpy(H.row_ptr).cuda(), torch.from_numpy(H.col).cuda(), torch.from_numpy(H.val).cuda(), H.n)
             for H, _ in items]
     taus = [t for _, t in items]
-    bplan = sexpm.BatchedPlan(devs, BATCH_EPS)
-    for r in bplan.compute(taus):      # warm-up
-        r.free()
-    torch.cuda.synchronize()
-    l0 = sexpm.kernel_launches()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        for r in bplan.compute(taus):
+
+    def run_batched(graph: int):
+        bplan = sexpm.BatchedPlan(devs, BATCH_EPS, batched_graph=graph)
+        for r in bplan.compute(taus):      # warm-up (captures the step graph, sizes the arena)
             r.free()
-    torch.cuda.synchronize()
-    t_batched = (time.perf_counter() - t0) / steps
-    l_batched = (sexpm.kernel_launches() - l0) // steps
-    bplan.close()
+        torch.cuda.synchronize()
+        l0 = sexpm.kernel_launches()
+        t0 = time.perf_counter()
+        st = None
+        for _ in range(steps):
+            res = bplan.compute(taus)
+            st = res[0].stats()
+            for r in res:
+                r.free()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / steps
+        launches = (sexpm.kernel_launches() - l0) // steps
+        info = bplan.graph_info()
+        bplan.close()
+        sexpm.release_memory()
+        sq = [x for x in st["steps"] if x["phase"] == 1]
+        return dt, launches, info, sum(x["products_done"] for x in sq), st["ms_squaring"], len(sq), st["peak_bytes"]
+
+    t_graph, l_graph, info, formed, sq_ms, nsq, peak_g = run_batched(1)
+    t_host, l_host, _, _, sq_ms_host, _, peak_h = run_batched(0)
     plans = [sexpm.Plan(d, BATCH_EPS) for d in devs]
     for p, t in zip(plans, taus):      # warm-up
         p.compute(t).free()
     torch.cuda.synchronize()
     l0 = sexpm.kernel_launches()
     t0 = time.perf_counter()
-    for _ in range(steps):
-        for p, t in zip(plans, taus):
-            p.compute(t).free()
+    for p, t in zip(plans, taus):
+        p.compute(t).free()
     torch.cuda.synchronize()
-    t_loop = (time.perf_counter() - t0) / steps
-    l_loop = (sexpm.kernel_launches() - l0) // steps
+    t_loop = time.perf_counter() - t0
+    l_loop = sexpm.kernel_launches() - l0
     for p in plans:
         p.close()
+    peak = 152 * 2 * 2 * 2.07  # GFLOP/s of the FP64 pipe (derived, as in the headline roofline)
+    gflops = 2.0 * formed / (sq_ms * 1e6) if sq_ms > 0 else 0.0
     return {"workload": "256 2-D Dirichlet Laplacians, side ~ U{16..128}, tau log-uniform [1e-4, 1e-2], eps 1e-12",
-            "n_total": int(sum(H.n for H, _ in items)), "batched_ms": 1000.0 * t_batched,
-            "per_matrix_loop_ms": 1000.0 * t_loop, "speedup_vs_loop": t_loop / t_batched,
-            "launches_batched": int(l_batched), "launches_loop": int(l_loop), "steps": steps}
+            "n_total": int(sum(H.n for H, _ in items)), "batched_ms": 1000.0 * t_graph,
+            "batched_host_driven_ms": 1000.0 * t_host, "per_matrix_loop_ms": 1000.0 * t_loop,
+            "speedup_vs_loop": t_loop / t_graph, "launches_batched": int(l_graph),
+            "launches_batched_host_driven": int(l_host), "launches_loop": int(l_loop),
+            "graph": {"squaring_steps": nsq, "graph_launches_per_batch": nsq - info["host_steps"],
+                      "kernels_per_step": info["kernels_per_step"], "kernels_per_alg41_pass": info["kernels_per_pass"],
+                      "arena_bytes": info["arena_bytes"], "resumed_steps": info["reruns"],
+                      "host_driven_steps": info["host_steps"]},
+            "peak_bytes_graph": int(peak_g), "peak_bytes_host_driven": int(peak_h),
+            "squaring_products_formed": int(formed), "squaring_ms": sq_ms, "squaring_ms_host_driven": sq_ms_host,
+            "squaring_fp64_gflops": gflops, "squaring_fp64_frac": gflops / peak, "steps": steps}
 
 
 def measure_adjoint(sexpm, torch, fd_edges: int = 0):

@@ -104,6 +104,14 @@ typedef struct {
                                of (M, N) (sexpm_choose_MN_refined), in r_0 = rho(M, h_{M,N}) and in
                                eps_g^(0) = a r_0 / (M e^{2 h_{M,N}}) */
   int32_t refine_kmax;      /* highest power of tau H the refined norm uses (odd, >= 3; default 41) */
+  int32_t batched_graph;    /* batched plans: 1 (default): the squaring phase runs as one captured CUDA
+                               graph per step -- sizes decided on the device, Algorithm 4.1 iterated
+                               by a conditional WHILE node, a fixed-capacity device arena held by the
+                               plan, grown when a product does not fit (the run resumes at that step);
+                               if device memory runs out the remaining steps run as host-driven
+                               launches; 0: host-driven launches.  Both give bit-identical results. */
+  int64_t batch_arena_bytes; /* first arena size for batched_graph = 1 (0, default: a few times T^_0,
+                               grown by the run; never more than the instances' dense size) */
 } sexpm_options;
 
 typedef struct sexpm_plan sexpm_plan_t;
@@ -236,7 +244,9 @@ int sexpm_choose_MN_refined(double norm_H, const double* pnorms, int32_t kmax, d
 
 /* Many independent matrices H_b (b = 0..count-1, sizes may differ) planned together: the
  * instances are stored as one block-diagonal matrix, so every step of Algorithm 4.2 runs as one
- * set of kernel launches for the whole batch.  Validation, symmetry and normality are per
+ * set of kernel launches for the whole batch (the sparse product's row kernels are persistent
+ * over per-size-class row lists that hold the rows of every instance); with
+ * sexpm_options.batched_graph = 1 each squaring step is one replay of a captured CUDA graph.  Validation, symmetry and normality are per
  * instance.  eps is shared.  Not in the paper (a batched form of Algorithm 4.2). */
 int sexpm_plan_batched(const sexpm_csr_view* Hs, int32_t count, double eps, const sexpm_options* opt,
                        void* stream, sexpm_plan_t** out);
@@ -247,6 +257,25 @@ int sexpm_plan_batched(const sexpm_csr_view* Hs, int32_t count, double eps, cons
  * steps.  outs[b] receives e^{tau_b H_b} (an n_b x n_b result).  For a plain plan this
  * is sexpm_compute with taus[0]. */
 int sexpm_compute_batched(sexpm_plan_t* plan, const double* taus, sexpm_result_t** outs);
+
+/* The captured squaring step of a batched plan (batched_graph = 1): device arena bytes held by
+ * the plan, graph captures so far, steps resumed after an arena overflow, squaring steps left to
+ * the host-driven launches because device memory ran out, kernels each step launches outside the
+ * Algorithm 4.1 loop and per pass of that loop.  Zeros before the first compute.  Any output may
+ * be NULL.  Not in the paper. */
+int sexpm_batched_graph_info(const sexpm_plan_t* plan, int64_t* arena_bytes, int32_t* captures, int32_t* reruns,
+                             int32_t* host_steps, int64_t* kernels_per_step, int64_t* kernels_per_pass);
+
+/* Autotuner of the numeric pass's accumulation layout for a batched plan: runs
+ * sexpm_compute_batched(plan, taus) once per candidate (ks_bytes[c]: the shared-memory budget of
+ * the k split, 0 = pure column split; wide[c]: 1024-thread blocks for the global-memory class)
+ * and keeps the fastest squaring phase for the plan's later computes.  ncand = 0 tries a built-in
+ * list (ks_bytes, wide) = (225280, 1), (112640, 1), (0, 1), (225280, 0).  ms_out (ncand entries
+ * or 4 for the built-in list; may be NULL) receives each candidate's squaring time, *best (may
+ * be NULL) the index chosen.  Results of every candidate agree to rounding (the layouts sum the
+ * same products in different orders).  Needs batched_graph = 1.  Not in the paper. */
+int sexpm_tune_batched(sexpm_plan_t* plan, const double* taus, int32_t ncand, const int32_t* ks_bytes,
+                       const int32_t* wide, double* ms_out, int32_t* best);
 
 /* ---------------------------------------------------------- adjoint form */
 

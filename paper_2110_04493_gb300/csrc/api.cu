@@ -79,7 +79,16 @@ void* Pool::alloc(size_t bytes, cudaStream_t s) {
   void* p = nullptr;
   if (g_fail_countdown.load() > 0 && g_fail_countdown.fetch_sub(1) == 1)
     fail(SEXPM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected by SEXPM_FAIL_ALLOC_AT)");
-  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool_for_current_device(), s);
+  cudaMemPool_t pool = pool_for_current_device();
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+  if (e == cudaErrorMemoryAllocation) {
+    // the pool keeps freed blocks (its release threshold is unbounded); blocks of other sizes may
+    // be what is missing: return them to the device and try once more
+    cudaGetLastError();
+    SX_CUDA(cudaDeviceSynchronize());
+    SX_CUDA(cudaMemPoolTrimTo(pool, 0));
+    e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     fail(e == cudaErrorMemoryAllocation ? SEXPM_ENOMEM : SEXPM_ECUDA,
@@ -415,6 +424,12 @@ struct sexpm_plan {
   // row schedule of the sparse products (empty: natural order)
   DevBuf<int32_t> sched;
   int64_t grid_stride = 0;
+  // batched plans: the captured squaring step and its arena (made on the first compute)
+  GraphSquaring* graph = nullptr;
+  int32_t layout_ks = -1, layout_wide = -1;  // accumulation layout chosen by sexpm_tune_batched
+  ~sexpm_plan() {
+    if (graph) graph_squaring_free(graph);
+  }
 };
 
 struct sexpm_result {
@@ -974,6 +989,8 @@ int sexpm_options_default(sexpm_options* opt) {
   opt->chunk_bytes = 0;
   opt->scaling = 0;
   opt->refine_kmax = 41;
+  opt->batched_graph = 1;
+  opt->batch_arena_bytes = 0;
   return SEXPM_OK;
 }
 
@@ -987,6 +1004,8 @@ static void check_options(const sexpm_options& o) {
   if (o.chunk_bytes < 0) fail(SEXPM_EINVAL, "chunk_bytes must be >= 0");
   if (o.scaling != 0 && o.scaling != 1) fail(SEXPM_EINVAL, "scaling must be 0 or 1");
   if (o.refine_kmax < 3) fail(SEXPM_EINVAL, "refine_kmax must be >= 3");
+  if (o.batched_graph != 0 && o.batched_graph != 1) fail(SEXPM_EINVAL, "batched_graph must be 0 or 1");
+  if (o.batch_arena_bytes < 0) fail(SEXPM_EINVAL, "batch_arena_bytes must be >= 0");
 }
 
 int sexpm_plan(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_options* opt, void* stream,
@@ -1494,11 +1513,53 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
   const double ms_taylor = t_tay.ms();
   // step 4: squarings; instance b is frozen (copied through) once its N_b squarings are done
   Timer t_sq(s);
+  // the captured step first (all N_max squarings unless device memory runs out; the
+  // host-driven launches below then do the rest from the last completed step)
+  const bool use_graph = o.batched_graph != 0 && Nmax > 0 && Nmax <= 128;
+  GraphSquaringOut gout;
+  int g_start = 1;
+  if (use_graph) {
+    if (!p->graph) p->graph = graph_squaring_new();
+    graph_squaring_set_layout(p->graph, p->layout_ks, p->layout_wide);
+    GraphSquaringIn gi;
+    gi.count = count;
+    gi.n = n;
+    gi.inst = inst;
+    gi.seg = seg;
+    gi.N = N;
+    gi.a = a;
+    gi.r0 = r0;
+    gi.nb.resize(count);
+    for (int b = 0; b < count; ++b) {
+      const int64_t nb = p->row0[b + 1] - p->row0[b];
+      gi.nb[b] = (double)nb;
+      gi.n_max = std::max(gi.n_max, nb);
+      gi.dense += nb * nb;
+    }
+    gi.arena_bytes = o.batch_arena_bytes;
+    gi.sym = sym;
+    gi.square_scale = o.square_scale != 0;
+    gi.e_r = o.e_r;
+    gi.max_iters = o.max_filter_iters;
+    graph_squarings(p->graph, T.view(), gi, gout, s);
+    for (const auto& st : gout.steps) steps.push_back(st);
+    g_start = gout.steps_done + 1;
+    if (gout.steps_done < Nmax) {
+      if (gout.steps_done > 0) {
+        CsrOwned Tg;
+        copy_csr(gout.T, s, Tg);
+        T = std::move(Tg);
+      }
+      graph_squaring_release(p->graph);
+      graph_squaring_note_host_steps(p->graph, Nmax - gout.steps_done);
+    }
+  }
+  const bool graph_result = use_graph && gout.steps_done == Nmax;
   RowStats rs;
   DevBuf<uint8_t> frozen_inst(count, s), frozen_row(n ? n : 1, s);
   std::vector<uint8_t> fz(count);
   std::vector<double> sq(count), tr(count);
-  for (int g = 1; g <= Nmax; ++g) {
+  for (int g = graph_result ? Nmax + 1 : g_start; g <= Nmax; ++g) {
     Timer ts(s);
     for (int b = 0; b < count; ++b) fz[b] = N[b] < g ? 1 : 0;
     SX_CUDA(cudaMemcpyAsync(frozen_inst.p, fz.data(), count, cudaMemcpyHostToDevice, s));
@@ -1556,8 +1617,21 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
   // step 5: e^{tau_b H_b} = I + T^_{N_b}, then one result per instance
   Timer t_fin(s);
   CsrOwned E;
-  add_identity(T.view(), s, E, hs);
   T.rp.free(); T.ci.free(); T.v.free();
+  if (graph_result) {
+    try {
+      add_identity(gout.T, s, E, hs);
+    } catch (const Error& e) {
+      if (e.code != SEXPM_ENOMEM) throw;
+      // the arena's work buffers make room for the result, T^_N stays (it is the input)
+      CsrOwned Tg;
+      copy_csr(gout.T, s, Tg);
+      graph_squaring_release(p->graph);
+      add_identity(Tg.view(), s, E, hs);
+    }
+  } else {
+    add_identity(T.view(), s, E, hs);
+  }
   gather_row_ptr(E.rp.p, seg, count, bnd.data(), s);
   std::vector<sexpm_result*> res(count, nullptr);
   try {
@@ -1596,6 +1670,58 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
     throw;
   }
   for (int b = 0; b < count; ++b) outs[b] = res[b];
+  SX_API_END
+}
+
+int sexpm_batched_graph_info(const sexpm_plan_t* p, int64_t* arena_bytes, int32_t* captures, int32_t* reruns,
+                             int32_t* host_steps, int64_t* kernels_per_step, int64_t* kernels_per_pass) {
+  SX_API_BEGIN
+  if (!p) fail(SEXPM_EINVAL, "null plan");
+  graph_squaring_info(p->graph, arena_bytes, captures, reruns, host_steps, kernels_per_step, kernels_per_pass);
+  SX_API_END
+}
+
+int sexpm_tune_batched(sexpm_plan_t* p, const double* taus, int32_t ncand, const int32_t* ks_bytes,
+                       const int32_t* wide, double* ms_out, int32_t* best) {
+  SX_API_BEGIN
+  if (!p || !taus) fail(SEXPM_EINVAL, "null argument");
+  if (p->count == 0) fail(SEXPM_EINVAL, "the tuner takes a batched plan");
+  if (p->opt.batched_graph == 0) fail(SEXPM_EINVAL, "the tuner sets the layout of the captured step (batched_graph = 1)");
+  if (ncand < 0 || (ncand > 0 && (!ks_bytes || !wide))) fail(SEXPM_EINVAL, "bad candidate list");
+  static const int32_t kKs[4] = {225280, 112640, 0, 225280};
+  static const int32_t kWide[4] = {1, 1, 1, 0};
+  const int nc = ncand ? ncand : 4;
+  const int32_t* ks = ncand ? ks_bytes : kKs;
+  const int32_t* wd = ncand ? wide : kWide;
+  for (int c = 0; c < nc; ++c)
+    if (ks[c] < 0 || ks[c] > (1 << 20) || (wd[c] != 0 && wd[c] != 1)) fail(SEXPM_EINVAL, "bad candidate");
+  const int32_t ks0 = p->layout_ks, w0 = p->layout_wide;
+  std::vector<sexpm_result_t*> outs(p->count, nullptr);
+  double best_ms = std::numeric_limits<double>::infinity();
+  int bi = 0;
+  for (int c = 0; c < nc; ++c) {
+    p->layout_ks = ks[c];
+    p->layout_wide = wd[c];
+    const int rc = sexpm_compute_batched(p, taus, outs.data());
+    if (rc != SEXPM_OK) {
+      p->layout_ks = ks0;
+      p->layout_wide = w0;
+      return rc;
+    }
+    const double ms = outs[0]->st.ms_squaring;
+    for (auto*& r : outs) {
+      sexpm_result_free(r);
+      r = nullptr;
+    }
+    if (ms_out) ms_out[c] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      bi = c;
+    }
+  }
+  p->layout_ks = ks[bi];
+  p->layout_wide = wd[bi];
+  if (best) *best = bi;
   SX_API_END
 }
 

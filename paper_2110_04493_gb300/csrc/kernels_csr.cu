@@ -275,7 +275,10 @@ __global__ void k_transpose_scatter(CsrD A, const int64_t* rp_t, int32_t* cursor
 
 // Algorithm 4.1 pass with a threshold per instance: row_part[i] = sum_{|v| <= t_inst} v^2 over
 // row i, keep[i] = #{|v| > t_inst}.  One warp per row.
-__global__ void k_filter_pass_seg(CsrD A, const int32_t* inst, const double* t_inst, int32_t* keep, double* row_part) {
+// A non-null `status` that is set means A was not formed (a capacity was exceeded): nothing runs.
+__global__ void k_filter_pass_seg(CsrD A, const int32_t* inst, const double* t_inst, int32_t* keep, double* row_part,
+                                  const int32_t* status) {
+  if (status && *status) return;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
     const unsigned long long tb = bits_of(t_inst[inst[i]]);
@@ -305,7 +308,8 @@ __global__ void k_seg_sum(const double* x, const int64_t* seg, double* out) {
 }
 
 __global__ void k_compact_seg(CsrD A, const int32_t* inst, const double* t_inst, const int64_t* rp_out, int32_t* ci_out,
-                              double* v_out) {
+                              double* v_out, const int32_t* status) {
+  if (status && *status) return;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const unsigned lt = (1u << lane_id()) - 1u;
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < A.n; i += nw) {
@@ -539,6 +543,17 @@ int64_t scan_counts(const int32_t* cnt, int64_t n, int64_t* rp, cudaStream_t s, 
   return hs.i[0];
 }
 
+int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+void scan_counts_dev(const int32_t* cnt, int64_t n, int64_t* rp, int64_t* ts, cudaStream_t s) {
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(cnt, n, ts);
+  k_scan_tile_sums<<<1, 1024, 0, s>>>(ts, tiles, ts + tiles);
+  k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, s>>>(cnt, n, ts, rp);
+  SX_CUDA(cudaGetLastError());
+  count_launches(3);
+}
+
 void add(const CsrD& A, const CsrD& B, double beta, cudaStream_t s, CsrOwned& C, HostScalars& hs) {
   const int64_t n = A.n;
   C.n = n;
@@ -620,17 +635,39 @@ void filter_pass_seg(const CsrD& A, const int32_t* inst, const double* t_inst, i
                      const int64_t* seg, int count, double* sums_host, cudaStream_t s) {
   if (A.n) {
     const int blocks = (int)std::min<int64_t>((A.n + 7) / 8, (int64_t)sm_count() * 64);
-    k_filter_pass_seg<<<blocks, 256, 0, s>>>(A, inst, t_inst, keep, row_part);
+    k_filter_pass_seg<<<blocks, 256, 0, s>>>(A, inst, t_inst, keep, row_part, nullptr);
     SX_CUDA(cudaGetLastError());
     count_launches(1);
   }
   seg_sums(row_part, seg, count, sums_host, s);
 }
 
+void seg_sums_dev(const double* x, const int64_t* seg, int count, double* out, cudaStream_t s) {
+  k_seg_sum<<<count, 256, 0, s>>>(x, seg, out);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+void filter_pass_seg_dev(const CsrD& A, const int32_t* inst, const double* t_inst, int32_t* keep, double* row_part,
+                         const int32_t* status, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((A.n + 7) / 8, (int64_t)sm_count() * 64);
+  k_filter_pass_seg<<<blocks, 256, 0, s>>>(A, inst, t_inst, keep, row_part, status);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+void compact_seg_dev(const CsrD& A, const int32_t* inst, const double* t_inst, const int64_t* rp_out, int32_t* ci_out,
+                     double* v_out, const int32_t* status, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((A.n + 7) / 8, (int64_t)sm_count() * 64);
+  k_compact_seg<<<blocks, 256, 0, s>>>(A, inst, t_inst, rp_out, ci_out, v_out, status);
+  SX_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
 void compact_seg(const CsrD& A, const int32_t* inst, const double* t_inst, CsrOwned& C, cudaStream_t s) {
   if (A.n == 0) return;
   const int blocks = (int)std::min<int64_t>((A.n + 7) / 8, (int64_t)sm_count() * 64);
-  k_compact_seg<<<blocks, 256, 0, s>>>(A, inst, t_inst, C.rp.p, C.ci.p, C.v.p);
+  k_compact_seg<<<blocks, 256, 0, s>>>(A, inst, t_inst, C.rp.p, C.ci.p, C.v.p, nullptr);
   SX_CUDA(cudaGetLastError());
   count_launches(1);
 }

@@ -204,7 +204,9 @@ __global__ void k_wcount(CsrD X, int32_t* cnt) {
 }
 
 // Writes the word pattern: distinct words and the OR of their column bits.
-__global__ void k_wwrite(CsrD X, const int64_t* wrp, int32_t* wi, uint32_t* wb) {
+// A non-null status that is set (the pattern exceeds its capacity) stops the kernel.
+__global__ void k_wwrite(CsrD X, const int64_t* wrp, int32_t* wi, uint32_t* wb, const int32_t* status) {
+  if (status && *status) return;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const unsigned lt = (1u << lane_id()) - 1u;
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < X.n; i += nw) {
@@ -464,12 +466,14 @@ __device__ __forceinline__ long long next_row(unsigned long long* ctr) {
 
 template <bool GLOBAL>
 __global__ void k_symbolic(CsrD A, WPat WB, WPat WD, bool hasD, const uint8_t* frozen, const int32_t* rows,
-                           int64_t nrows, const int32_t* base, const int32_t* words, int32_t* cnt, int32_t* cnt_up,
-                           uint32_t* gscratch, int64_t gstride, unsigned long long* row_ctr) {
+                           int64_t nrows, const unsigned long long* nrows_dev, const int32_t* base,
+                           const int32_t* words, int32_t* cnt, int32_t* cnt_up, uint32_t* gscratch, int64_t gstride,
+                           unsigned long long* row_ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int red[32];
   __shared__ long long s_next;
   uint32_t* bm = GLOBAL ? gscratch + (int64_t)blockIdx.x * gstride : reinterpret_cast<uint32_t*>(smem);
+  if (nrows_dev) nrows = min(nrows, (int64_t)*nrows_dev);  // list length decided on the device
   long long nxt = 0;
   for (int64_t r = blockIdx.x; r < nrows;) {
     if (threadIdx.x == 0) nxt = next_row(row_ctr);
@@ -841,7 +845,8 @@ __device__ void numeric_row(const CsrD& A, const CsrD& B, const CsrD& D, double 
 template <bool GLOBAL, int NT>
 __global__ void __launch_bounds__(NT, (8 * SEXPM_NUMERIC_BLOCKS * 32) / NT) k_numeric(CsrD A, CsrD B, CsrD D, WPat WB, WPat WD, double div, double beta, bool upper,
                           const uint8_t* frozen, const int32_t* cnt_up, const int32_t* rows,
-                          int64_t nrows, const int32_t* base, const int32_t* words, const int64_t* rp_out,
+                          int64_t nrows, const unsigned long long* nrows_dev, const int32_t* base,
+                          const int32_t* words, const int64_t* rp_out,
                           int32_t* ci_out, double* v_out, double* row_sq, double* row_diag, unsigned char* gscratch,
                           int64_t gstride, unsigned long long* work_total, unsigned long long* row_ctr,
                           int ks_bytes, int64_t out_base) {
@@ -853,6 +858,7 @@ __global__ void __launch_bounds__(NT, (8 * SEXPM_NUMERIC_BLOCKS * 32) / NT) k_nu
   unsigned char* mem = GLOBAL ? gscratch + (int64_t)blockIdx.x * gstride : smem;
   const int T = blockDim.x;
   const bool hasD = D.n > 0;
+  if (nrows_dev) nrows = min(nrows, (int64_t)*nrows_dev);  // list length decided on the device
   long long nxt = 0;
   for (int64_t r = blockIdx.x; r < nrows;) {
     if (threadIdx.x == 0) nxt = next_row(row_ctr);
@@ -886,7 +892,9 @@ __global__ void __launch_bounds__(NT, (8 * SEXPM_NUMERIC_BLOCKS * 32) / NT) k_nu
 // Fills the entries below the diagonal of a structurally symmetric product whose upper part
 // (columns >= row) was computed: C[i][j] = C[j][i] for j < i, found in row j.
 // One warp per row.  A partner that is absent (the pattern was not symmetric) counts a miss.
-__global__ void k_mirror(int64_t n, const int64_t* rp, const int32_t* ci, double* v, unsigned long long* misses) {
+__global__ void k_mirror(int64_t n, const int64_t* rp, const int32_t* ci, double* v, unsigned long long* misses,
+                         const int32_t* status) {
+  if (status && *status) return;  // the product was not formed (capacity exceeded)
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < n; i += nw) {
     const int64_t p0 = rp[i], p1 = rp[i + 1];
@@ -1023,9 +1031,36 @@ void word_pattern(const CsrD& X, cudaStream_t s, WPatOwned& out, HostScalars& hs
   const int64_t total = scan_counts(cnt.p, n, out.rp.p, s, hs);
   out.wi.reset(total, s);
   out.wb.reset(total, s);
-  k_wwrite<<<blocks, 256, 0, s>>>(X, out.rp.p, out.wi.p, out.wb.p);
+  k_wwrite<<<blocks, 256, 0, s>>>(X, out.rp.p, out.wi.p, out.wb.p, nullptr);
   SX_CUDA(cudaGetLastError());
   count_launches(1);
+}
+
+// ---- device-sized products (the captured batched step)
+// status |= bit when the size at *rp_n exceeds cap; need = the largest size requested.  Skipped
+// once the status is set (an earlier step stopped the run: its sizes are not this run's).
+__global__ void k_dev_cap_check(const int64_t* rp_n, int64_t cap, int32_t* status, unsigned long long* need,
+                                int32_t bit) {
+  if (*status) return;
+  const long long total = *rp_n;
+  atomicMax(need, (unsigned long long)total);
+  if (total > cap) atomicOr(status, bit);
+}
+
+// Before a pass over the row lists: a row whose need exceeds the global class's scratch stride
+// (a bound the buffers were sized by) stops the step; when the step is stopped every list is
+// emptied so the row kernels form nothing.
+__global__ void k_dev_gate(unsigned long long* counts, const unsigned long long* maxneed, long long global_cap,
+                           int32_t* status) {
+  if (threadIdx.x != 0) return;
+  if (counts[kClasses - 1] > 0 && maxneed[kClasses - 1] > (unsigned long long)global_cap) atomicOr(status, kStBound);
+  if (*status)
+    for (int c = 0; c < kClasses; ++c) counts[c] = 0;
+}
+
+// Sets status bit `bit` when *x != 0.
+__global__ void k_dev_flag_nonzero(const unsigned long long* x, int32_t* status, int32_t bit) {
+  if (threadIdx.x == 0 && *x) atomicOr(status, bit);
 }
 
 // Arguments of one numeric launch (one size class).
@@ -1038,6 +1073,7 @@ struct NumericArgs {
   const int32_t* cnt_up;
   const int32_t* rows;
   int64_t nrows;
+  const unsigned long long* nrows_dev;  // non-null: the list length is read on the device
   const int32_t* base;
   const int32_t* words;
   const int64_t* rp_out;
@@ -1060,7 +1096,8 @@ void launch_numeric(const NumericArgs& a, int threads, int bytes, cudaStream_t s
   // (the 64- and 128-thread classes run the 256-thread instance with fewer threads)
   if (grid == 0) grid = std::min<int64_t>(a.nrows, resident_blocks(k_numeric<GLOBAL, NT>, threads, bytes));
   k_numeric<GLOBAL, NT><<<(unsigned)grid, threads, bytes, s>>>(
-      a.A, a.B, a.D, a.WB, a.WD, a.div, a.beta, a.upper, a.frozen, a.cnt_up, a.rows, a.nrows, a.base, a.words,
+      a.A, a.B, a.D, a.WB, a.WD, a.div, a.beta, a.upper, a.frozen, a.cnt_up, a.rows, a.nrows, a.nrows_dev, a.base,
+      a.words,
       a.rp_out, a.ci_out, a.v_out, a.row_sq, a.row_diag, a.gscratch, a.gstride, a.work_total, a.row_ctr,
       a.ks_bytes, a.out_base);
 }
@@ -1138,7 +1175,7 @@ void product_symbolic(const CsrD& A, const CsrD& B, const CsrD& D, bool upper, c
         const int bytes = (int)((need + 1023) & ~1023ll);
         const int64_t grid = std::min<int64_t>(nr, resident_blocks(k_symbolic<false>, threads, bytes));
         k_symbolic<false><<<(unsigned)grid, threads, bytes, s>>>(A, WB, WD, ps.hasD, frozen, ps.lists.p + c * n, nr,
-                                                               ps.base.p, ps.words.p, ps.cnt.p,
+                                                               nullptr, ps.base.p, ps.words.p, ps.cnt.p,
                                                                upper ? ps.cnt_up.p : nullptr, nullptr, 0,
                                                                ps.row_ctr.p + c);
       } else {
@@ -1146,7 +1183,7 @@ void product_symbolic(const CsrD& A, const CsrD& B, const CsrD& D, bool upper, c
         const int64_t grid = std::min<int64_t>(nr, (int64_t)sms * 2);
         gs.reset((size_t)(stride * grid), s);
         k_symbolic<true><<<(unsigned)grid, threads, 0, s>>>(A, WB, WD, ps.hasD, frozen, ps.lists.p + c * n, nr,
-                                                          ps.base.p, ps.words.p, ps.cnt.p,
+                                                          nullptr, ps.base.p, ps.words.p, ps.cnt.p,
                                                           upper ? ps.cnt_up.p : nullptr, gs.p, stride,
                                                           ps.row_ctr.p + c);
       }
@@ -1185,7 +1222,7 @@ int64_t product_numeric(ProductSym& ps, const CsrD& A, const CsrD& B, const CsrD
     const int threads = wide ? kNumThreadsWide[c] : kClassThreads[c];
     const int64_t need = (int64_t)h[kClasses + c];
     NumericArgs na{A, B, D, WB, WD, div, beta, upper, ps.frozen, upper ? ps.cnt_up.p : nullptr, ps.lists.p + c * n, nr,
-                   ps.base.p, ps.words.p, ps.row_ptr(), ci_out, v_out, stats ? stats->sq.p : nullptr,
+                   nullptr, ps.base.p, ps.words.p, ps.row_ptr(), ci_out, v_out, stats ? stats->sq.p : nullptr,
                    stats ? stats->diag.p : nullptr, nullptr, 0, ps.ctr.p + 2 * kClasses + 3,
                    ps.row_ctr.p + kClasses + c, ps.ks_bytes, out_base};
     if (c < kClasses - 1) {
@@ -1220,7 +1257,7 @@ void mirror_lower(const CsrOwned& C, cudaStream_t s, HostScalars& hs) {
   DevBuf<unsigned long long> miss(1, s);
   SX_CUDA(cudaMemsetAsync(miss.p, 0, sizeof(unsigned long long), s));
   const int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)num_sms() * 64);
-  k_mirror<<<blocks, 256, 0, s>>>(n, C.rp.p, C.ci.p, C.v.p, miss.p);
+  k_mirror<<<blocks, 256, 0, s>>>(n, C.rp.p, C.ci.p, C.v.p, miss.p, nullptr);
   SX_CUDA(cudaGetLastError());
   count_launches(1);
   unsigned long long h = 0;
@@ -1253,6 +1290,141 @@ int64_t spgemm(const CsrD& A, const CsrD& B, const CsrD& D, double div, double b
   if (upper) mirror_lower(C, s, hs);
   if (times) times->ms_numeric += ev_num.stop();
   return ps.products;
+}
+
+// ---------------------------------------------------------------- device-sized product
+// The same kernels as spgemm, launched with grids and shared-memory sizes that do not depend on
+// the data: the size classes use their class's full shared-memory budget, the persistent
+// row kernels read their list lengths on the device, and the global-memory class uses scratch
+// sized for the widest row an instance of n_max rows can have.  Nothing is read back, so the
+// sequence can be captured into a CUDA graph.  Results equal spgemm's bit for bit (the
+// accumulation layout of a row depends only on the row and its class).
+
+namespace {
+constexpr int kCtrHalf = 2 * kClasses + 4;  // counters per half of DevProduct::ctr
+}  // namespace
+
+int default_ks_bytes() { return ksplit_bytes(); }
+bool default_wide_blocks() { return wide_blocks(); }
+
+int dev_product_products_index() { return 2 * kClasses + 2; }
+int dev_product_formed_index() { return kCtrHalf + 2 * kClasses + 3; }
+
+void dev_product_scratch(int64_t n_max, int ks_bytes, bool wide, int64_t& sym_stride, int64_t& sym_grid,
+                         int64_t& num_stride, int64_t& num_grid) {
+  // A row of an instance with n_max rows spans at most n_max columns from a 32-aligned base:
+  // W <= n_max / 32 + 2 bitmap words and at most n_max entries.
+  const int64_t W = n_max / 32 + 2;
+  sym_stride = (W + 63) & ~63ll;  // uint32 words (the symbolic need is 4 W bytes)
+  sym_grid = (int64_t)num_sms() * 2;
+  // numeric: the k split keeps a row within ks_bytes * warps / 32 unless one accumulator does
+  // not fit, so the need is at most max(that budget, the need of one accumulator)
+  const int threads = wide ? kNumThreadsWide[kClasses - 1] : kClassThreads[kClasses - 1];
+  const long long one = need_bytes(W, n_max, n_max, 1);
+  const long long need = std::max<long long>((long long)ks_bytes * (threads / 32) / kNumericWarpsPerSM, one);
+  num_stride = (need + 255) & ~255ll;
+  num_grid = (int64_t)num_sms() * (threads >= 1024 ? 1 : 2);
+}
+
+void dev_product_prepare(DevProduct& P) {
+  set_smem_limits();
+  for (int c = 0; c < kClasses - 1; ++c) {
+    const int bytes = class_limit(c);
+    P.grid_sym[c] = resident_blocks(k_symbolic<false>, kClassThreads[c], bytes);
+    const int threads = P.wide ? kNumThreadsWide[c] : kClassThreads[c];
+    P.grid_num[c] = threads <= 256   ? resident_blocks(k_numeric<false, 256>, threads, bytes)
+                    : threads == 512 ? resident_blocks(k_numeric<false, 512>, threads, bytes)
+                                     : resident_blocks(k_numeric<false, 1024>, threads, bytes);
+  }
+  P.grid_sym[kClasses - 1] = P.gs_sym_grid;
+  P.grid_num[kClasses - 1] = P.gs_num_grid;
+  P.prepared = true;
+}
+
+void dev_product(const CsrD& A, const CsrD& B, bool hasD, double div, double beta, bool upper, const uint8_t* frozen,
+                 const DevProduct& P, cudaStream_t s) {
+  const int64_t n = P.n;
+  if (!P.prepared) fail(SEXPM_ECUDA, "dev_product: launch shapes not prepared");
+  const int sms = num_sms();
+  CsrD D;
+  if (hasD) D = B;
+  WPat WB;
+  WB.rp = P.wrp; WB.wi = P.wi; WB.wb = P.wb;
+  const WPat WD = hasD ? WB : WPat();
+  unsigned long long* cs = P.ctr;             // symbolic half
+  unsigned long long* cn = P.ctr + kCtrHalf;  // numeric half
+  SX_CUDA(cudaMemsetAsync(P.ctr, 0, 2 * kCtrHalf * sizeof(unsigned long long), s));
+  SX_CUDA(cudaMemsetAsync(P.row_ctr, 0, 2 * kClasses * sizeof(unsigned long long), s));
+  const int rblocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)sms * 64);
+  // word pattern of B, within its capacity
+  k_wcount<<<rblocks, 256, 0, s>>>(B, P.cnt);
+  SX_CUDA(cudaGetLastError());
+  scan_counts_dev(P.cnt, n, P.wrp, P.scan_ts, s);
+  k_dev_cap_check<<<1, 1, 0, s>>>(P.wrp + n, P.wcap, P.status, P.need_w, kStWords);
+  k_wwrite<<<rblocks, 256, 0, s>>>(B, P.wrp, P.wi, P.wb, P.status);
+  // analysis and symbolic classes
+  k_analysis<<<rblocks, 256, 0, s>>>(A, B, D, frozen, P.base, P.words, P.flops);
+  k_sum_i64<<<(unsigned)std::min<int64_t>((n + 255) / 256, sms * 8), 256, 0, s>>>(P.flops, n,
+                                                                               cs + dev_product_products_index());
+  k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nullptr, P.words, nullptr, nullptr, 0, P.ks_bytes, P.lists,
+                                                       n, cs, cs + kClasses, 0, n, false);
+  k_zero_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.words, n, P.row_sq, P.row_diag, P.cnt,
+                                                       upper ? P.cnt_up : nullptr);
+  k_dev_gate<<<1, 32, 0, s>>>(cs, cs + kClasses, 4 * P.gs_sym_stride, P.status);
+  SX_CUDA(cudaGetLastError());
+  count_launches(8);
+  for (int c = 0; c < kClasses; ++c) {
+    const int threads = kClassThreads[c];
+    if (c < kClasses - 1) {
+      const int bytes = class_limit(c);
+      k_symbolic<false><<<(unsigned)P.grid_sym[c], threads, bytes, s>>>(A, WB, WD, hasD, frozen, P.lists + c * n, n,
+                                                                       cs + c, P.base, P.words, P.cnt,
+                                                                       upper ? P.cnt_up : nullptr, nullptr, 0,
+                                                                       P.row_ctr + c);
+    } else {
+      k_symbolic<true><<<(unsigned)P.gs_sym_grid, threads, 0, s>>>(A, WB, WD, hasD, frozen, P.lists + c * n, n, cs + c,
+                                                                  P.base, P.words, P.cnt, upper ? P.cnt_up : nullptr,
+                                                                  P.gs_sym, P.gs_sym_stride, P.row_ctr + c);
+    }
+    SX_CUDA(cudaGetLastError());
+    count_launches(1);
+  }
+  // row pointers of the unfiltered product and its capacity
+  scan_counts_dev(P.cnt, n, P.rp_out, P.scan_ts, s);
+  k_dev_cap_check<<<1, 1, 0, s>>>(P.rp_out + n, P.cap_out, P.status, P.need, kStProduct);
+  const bool wide = P.wide;
+  k_classify<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nullptr, P.words, P.rp_out, upper ? P.cnt_up : nullptr, 1,
+                                                       P.ks_bytes, P.lists, n, cn, cn + kClasses, 0, n, wide);
+  k_dev_gate<<<1, 32, 0, s>>>(cn, cn + kClasses, P.gs_num_stride, P.status);
+  SX_CUDA(cudaGetLastError());
+  count_launches(3);
+  for (int c = 0; c < kClasses; ++c) {
+    const int threads = wide ? kNumThreadsWide[c] : kClassThreads[c];
+    NumericArgs na{A, B, D, WB, WD, div, beta, upper, frozen, upper ? P.cnt_up : nullptr, P.lists + c * n, n, cn + c,
+                   P.base, P.words, P.rp_out, P.ci_out, P.v_out, P.row_sq, P.row_diag, nullptr, 0,
+                   cn + 2 * kClasses + 3, P.row_ctr + kClasses + c, P.ks_bytes, 0};
+    if (c < kClasses - 1) {
+      const int bytes = class_limit(c);
+      if (threads <= 256) launch_numeric<false, 256>(na, threads, bytes, s, P.grid_num[c]);
+      else if (threads == 512) launch_numeric<false, 512>(na, threads, bytes, s, P.grid_num[c]);
+      else launch_numeric<false, 1024>(na, threads, bytes, s, P.grid_num[c]);
+    } else {
+      na.gscratch = P.gs_num;
+      na.gstride = P.gs_num_stride;
+      if (threads <= 256) launch_numeric<true, 256>(na, threads, 0, s, P.gs_num_grid);
+      else if (threads == 512) launch_numeric<true, 512>(na, threads, 0, s, P.gs_num_grid);
+      else launch_numeric<true, 1024>(na, threads, 0, s, P.gs_num_grid);
+    }
+    SX_CUDA(cudaGetLastError());
+    count_launches(1);
+  }
+  if (upper) {
+    unsigned long long* miss = cn + 2 * kClasses + 2;  // unused by the numeric classification
+    k_mirror<<<rblocks, 256, 0, s>>>(n, P.rp_out, P.ci_out, P.v_out, miss, P.status);
+    k_dev_flag_nonzero<<<1, 32, 0, s>>>(miss, P.status, kStMirror);
+    SX_CUDA(cudaGetLastError());
+    count_launches(2);
+  }
 }
 
 }  // namespace sexpm

@@ -289,6 +289,122 @@ void block_put(const CsrD& X, int64_t row0, int64_t nnz0, int64_t* rp, int32_t* 
 void block_get(const CsrD& E, int64_t row0, int64_t nb, int64_t nnz_b, CsrOwned& out, cudaStream_t s);
 void gather_row_ptr(const int64_t* rp, const int64_t* seg, int count, int64_t* out_host, cudaStream_t s);
 
+// Device-only forms for a step whose sizes are decided on the device (the captured batched
+// squaring step): no host read-back, grids independent of the data.
+int64_t scan_tiles(int64_t n);  // int64 scratch values scan_counts_dev needs
+// Exclusive scan into rp (n + 1 entries; the total stays on the device at rp[n]).
+void scan_counts_dev(const int32_t* cnt, int64_t n, int64_t* rp, int64_t* ts, cudaStream_t s);
+// out[b] = sum over instance b's rows of x (device out).
+void seg_sums_dev(const double* x, const int64_t* seg, int count, double* out, cudaStream_t s);
+// One Algorithm 4.1 pass with thresholds t_inst[b]: keep[i], row_part[i]; skipped while *status != 0.
+void filter_pass_seg_dev(const CsrD& A, const int32_t* inst, const double* t_inst, int32_t* keep, double* row_part,
+                         const int32_t* status, cudaStream_t s);
+// A~ = A - b_n into rp_out/ci_out/v_out; skipped while *status != 0.
+void compact_seg_dev(const CsrD& A, const int32_t* inst, const double* t_inst, const int64_t* rp_out, int32_t* ci_out,
+                     double* v_out, const int32_t* status, cudaStream_t s);
+
+// Status bits of a device-sized step.
+constexpr int32_t kStProduct = 1;   // the unfiltered product exceeded its capacity
+constexpr int32_t kStFiltered = 2;  // the filtered product exceeded its capacity
+constexpr int32_t kStMirror = 4;    // symmetric mode: an entry without its mirror partner
+constexpr int32_t kStNoConv = 8;    // Algorithm 4.1 reached its iteration cap
+constexpr int32_t kStBound = 16;    // a row exceeded the scratch bound of its size class
+constexpr int32_t kStWords = 32;    // the word pattern of B exceeded its capacity
+
+// Buffers of C = (A B)/div + beta D formed with sizes decided on the device: every buffer is
+// allocated beforehand (capacities in entries), B and D share one pattern (D is B or absent).
+struct DevProduct {
+  int64_t n = 0;
+  int64_t* wrp = nullptr;           // word pattern of B: n + 1 row pointers,
+  int32_t* wi = nullptr;            // word indices and
+  uint32_t* wb = nullptr;           // masks (wcap words)
+  int64_t wcap = 0;
+  int32_t *base = nullptr, *words = nullptr, *cnt = nullptr, *cnt_up = nullptr;  // per row
+  int32_t* lists = nullptr;         // kProductClasses x n row lists
+  int64_t* flops = nullptr;         // per row
+  unsigned long long* ctr = nullptr;      // 2 (2 kProductClasses + 4) counters: symbolic half, numeric half
+  unsigned long long* row_ctr = nullptr;  // 2 kProductClasses
+  int64_t* scan_ts = nullptr;       // scan_tiles(n)
+  uint32_t* gs_sym = nullptr;       // global-class scratch of the symbolic pass (gs_sym_grid blocks)
+  int64_t gs_sym_stride = 0, gs_sym_grid = 0;   // (uint32 words per block)
+  unsigned char* gs_num = nullptr;  // global-class scratch of the numeric pass
+  int64_t gs_num_stride = 0, gs_num_grid = 0;   // (bytes per block)
+  int64_t* rp_out = nullptr;        // n + 1
+  int32_t* ci_out = nullptr;
+  double* v_out = nullptr;
+  int64_t cap_out = 0;
+  double *row_sq = nullptr, *row_diag = nullptr;  // per-row statistics of the product
+  int32_t* status = nullptr;        // kSt* bits (sticky)
+  unsigned long long* need = nullptr;    // largest unfiltered size requested
+  unsigned long long* need_w = nullptr;  // largest word pattern requested
+  int ks_bytes = 0;
+  bool wide = true;
+  int64_t grid_sym[kProductClasses] = {}, grid_num[kProductClasses] = {};  // set by dev_product_prepare
+  bool prepared = false;
+};
+// Scratch sizes of the global-memory class for rows of instances with at most n_max rows.
+void dev_product_scratch(int64_t n_max, int ks_bytes, bool wide, int64_t& sym_stride, int64_t& sym_grid,
+                         int64_t& num_stride, int64_t& num_grid);
+// Launch shapes of dev_product (occupancy queries and shared-memory limits, done before any
+// capture).
+void dev_product_prepare(DevProduct& P);
+// Enqueues the whole product (word pattern, analysis, classes, symbolic, scan, capacity checks,
+// numeric, mirror) on s without reading anything back: when a size exceeds its capacity the
+// numeric pass forms nothing and status gets the matching bit.
+void dev_product(const CsrD& A, const CsrD& B, bool hasD, double div, double beta, bool upper, const uint8_t* frozen,
+                 const DevProduct& P, cudaStream_t s);
+// Index of the products counter (symbolic half) and of the formed-products counter (numeric
+// half) in DevProduct::ctr.
+int dev_product_products_index();
+int dev_product_formed_index();
+// Accumulation layout defaults of the numeric pass (k-split byte budget, wide blocks for the
+// global-memory class), from the environment when set.
+int default_ks_bytes();
+bool default_wide_blocks();
+
+// ---------------------------------------------------------------- captured batched squarings
+// The squaring phase of a batched plan replayed as one captured CUDA graph per step (sizes
+// decided on the device, Algorithm 4.1 in a conditional WHILE node, a fixed-capacity arena that
+// is grown when a product does not fit, the run resuming at that step).
+struct GraphSquaring;
+struct GraphSquaringIn {
+  int count = 0;
+  int64_t n = 0;          // rows of the batch
+  int64_t n_max = 0;      // rows of its largest instance
+  int64_t dense = 0;      // sum of n_b^2 (no product is larger)
+  int64_t arena_bytes = 0;  // first arena budget (0: small, grown by the run)
+  const int32_t* inst = nullptr;  // device: instance of each row
+  const int64_t* seg = nullptr;   // device: first row of each instance (count + 1)
+  std::vector<int32_t> N;         // squarings per instance
+  std::vector<double> a, r0, nb;  // a_b, r_0,b and n_b per instance
+  bool sym = false, square_scale = true;
+  double e_r = 0.1;
+  int max_iters = 100;
+};
+struct GraphSquaringOut {
+  CsrD T;                 // T^ after steps_done squarings (block diagonal), in the arena
+  int steps_done = 0;     // squarings completed by the graph (all of them unless the arena ran out)
+  std::vector<sexpm_step_stats> steps;
+  int reruns = 0;
+  int64_t launches = 0;
+  int64_t arena_bytes = 0;
+};
+GraphSquaring* graph_squaring_new();
+void graph_squaring_free(GraphSquaring* G);
+// Releases the arena (the graph is captured again on the next run).
+void graph_squaring_release(GraphSquaring* G);
+// Arena bytes, graph captures, resumed steps after an arena overflow, squaring steps left to the
+// host-driven launches (device memory ran out), kernels per step outside the Algorithm 4.1 loop
+// and kernels per pass of that loop.
+void graph_squaring_info(const GraphSquaring* G, int64_t* arena_bytes, int32_t* captures, int32_t* reruns,
+                         int32_t* host_steps, int64_t* kernels_per_step, int64_t* kernels_per_pass);
+void graph_squaring_note_host_steps(GraphSquaring* G, int steps);
+// Accumulation layout of the numeric pass (ks_bytes < 0 / wide < 0: the defaults).
+void graph_squaring_set_layout(GraphSquaring* G, int ks_bytes, int wide);
+// Runs the squarings from T^_0 (T0, device, block diagonal).  Orders itself after s and s after it.
+void graph_squarings(GraphSquaring* G, const CsrD& T0, const GraphSquaringIn& in, GraphSquaringOut& out,
+                     cudaStream_t s);
+
 // ---------------------------------------------------------------- adjoint helpers
 // out[p] = (accumulate ? out[p] : 0) + alpha sum_l A_il B_jl + beta A_ij for every stored (i, j)
 // of P (out has P.nnz entries in P's order).

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
     _fields_ = [("e_r", ctypes.c_double), ("square_scale", ctypes.c_int32), ("normal_override", ctypes.c_int32),
                 ("max_filter_iters", ctypes.c_int32), ("n_extra", ctypes.c_int32), ("max_taylor", ctypes.c_int32),
                 ("symmetric", ctypes.c_int32), ("row_order", ctypes.c_int32), ("chunk_bytes", ctypes.c_int64),
-                ("scaling", ctypes.c_int32), ("refine_kmax", ctypes.c_int32)]
+                ("scaling", ctypes.c_int32), ("refine_kmax", ctypes.c_int32), ("batched_graph", ctypes.c_int32),
+                ("batch_arena_bytes", ctypes.c_int64)]
 
 
 class StepStats(ctypes.Structure):
@@ -98,6 +99,10 @@ def load() -> ctypes.CDLL:
                                P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_double)]
     L.sexpm_plan_batched.argtypes = [P(CsrView), ctypes.c_int32, ctypes.c_double, P(Options), vp, P(vp)]
     L.sexpm_compute_batched.argtypes = [vp, P(ctypes.c_double), P(vp)]
+    L.sexpm_batched_graph_info.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_int32),
+                                           P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_int64)]
+    L.sexpm_tune_batched.argtypes = [vp, P(ctypes.c_double), ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
+                                     P(ctypes.c_double), P(ctypes.c_int32)]
     L.sexpm_adjoint.argtypes = [vp, ctypes.c_double, P(CsrView), ctypes.c_int32, P(vp), P(vp)]
     L.sexpm_forward_keep.argtypes = [vp, ctypes.c_double, ctypes.c_int32, P(vp), P(vp)]
     L.sexpm_transpose.argtypes = [P(CsrView), vp, P(vp)]
@@ -384,6 +389,27 @@ class BatchedPlan:
         outs = (ctypes.c_void_p * self.count)()
         _check(load().sexpm_compute_batched(self._h, taus, outs))
         return [Result(outs[k]) for k in range(self.count)]
+
+    def graph_info(self) -> dict:
+        """sexpm_batched_graph_info: the captured squaring step's arena and counters."""
+        ab, kps, kpp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        cap, rer, hst = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().sexpm_batched_graph_info(self._h, ctypes.byref(ab), ctypes.byref(cap), ctypes.byref(rer),
+                                               ctypes.byref(hst), ctypes.byref(kps), ctypes.byref(kpp)))
+        return {"arena_bytes": ab.value, "captures": cap.value, "reruns": rer.value, "host_steps": hst.value,
+                "kernels_per_step": kps.value, "kernels_per_pass": kpp.value}
+
+    def tune(self, taus, candidates=None):
+        """sexpm_tune_batched over [(ks_bytes, wide), ...] (None: the library's list); returns
+        (squaring ms per candidate, index chosen)."""
+        taus_c = (ctypes.c_double * self.count)(*[float(t) for t in taus])
+        nc = len(candidates) if candidates else 0
+        ks = (ctypes.c_int32 * max(nc, 1))(*[int(c[0]) for c in candidates or []])
+        wd = (ctypes.c_int32 * max(nc, 1))(*[int(c[1]) for c in candidates or []])
+        ms = (ctypes.c_double * (nc if nc else 4))()
+        best = ctypes.c_int32()
+        _check(load().sexpm_tune_batched(self._h, taus_c, nc, ks, wd, ms, ctypes.byref(best)))
+        return list(ms), best.value
 
     def close(self) -> None:
         if self._h:

@@ -47,6 +47,7 @@ def test_options_default(lib):
     o = sexpm.options()
     assert (o.e_r, o.square_scale, o.normal_override, o.max_filter_iters, o.n_extra, o.symmetric, o.row_order) == \
         (0.1, 1, -1, 100, 50, 1, 1)
+    assert (o.batched_graph, o.batch_arena_bytes, o.scaling, o.refine_kmax) == (1, 0, 0, 41)
 
 
 def _rho_closed(M, x):
