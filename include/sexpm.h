@@ -184,6 +184,26 @@ int sexpm_compute(sexpm_plan_t* plan, double tau, sexpm_result_t** out);
 /* Dimension and stored-entry count of a result. */
 int sexpm_result_info(const sexpm_result_t* res, int64_t* n, int64_t* nnz);
 
+/* ---------------------------------------------------------- complex H
+ * The method is stated for H in C^{n x n}.  A complex CSR view has val pointing to 2 nnz doubles,
+ * the (re, im) pairs of the entries (the layout of C99 double complex / numpy complex128).
+ * Internally Z = X + iY is carried by the rows [X_i | -Y_i] of its real embedding
+ * [[X, -Y], [Y, X]] (products of the embedding are the embedding of the products), every
+ * product forms those n rows only, and Algorithm 4.1 keeps or drops a complex entry as a whole
+ * by its modulus |z| (its sums add |z|^2).  (M, N) come from ||tau H||_F with the complex norm;
+ * a = 1/(N+1) when H is normal (H H^* = H^* H: Hermitian and skew-Hermitian H exactly, else
+ * ||H H^* - H^* H||_F <= 64 u ||H||_F^2).  tau stays real (put a factor -i into H for e^{-i tau H}).
+ * The symmetric mode, the row chunking, the refined scaling (scaling = 1), the batched form,
+ * the adjoint and e^H R are real-only.  n <= 2^30.  sexpm_compute computes e^{tau H} of such a
+ * plan; its statistics count the real entries and products of the embedding's top rows. */
+int sexpm_plan_z(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_options* opt, void* stream,
+                 sexpm_plan_t** out);
+/* 1 when res holds a complex e^{tau H} (from a plan of sexpm_plan_z). */
+int sexpm_result_is_complex(const sexpm_result_t* res, int32_t* is_complex);
+/* Copy a complex result: n+1 row pointers, nnz columns, 2 nnz doubles (re, im pairs).
+ * SEXPM_EINVAL for a real result (and sexpm_result_copy returns SEXPM_EINVAL for a complex one). */
+int sexpm_result_copy_z(const sexpm_result_t* res, int64_t* row_ptr, int32_t* col, double* val, int32_t on_device);
+
 /* Copy a result into caller buffers of n+1 / nnz / nnz elements; on_device
  * selects device (1) or host (0) destination pointers. */
 int sexpm_result_copy(const sexpm_result_t* res, int64_t* row_ptr, int32_t* col, double* val,

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsexpm.so")
 SOURCES = ["api.cu", "kernels_spgemm.cu", "kernels_csr.cu", "kernels_filter.cu", "kernels_adjoint.cu", "kernels_spmm.cu",
-           "batched_graph.cu",
+           "batched_graph.cu", "complex_path.cu",
            "noalloc.cu", "plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

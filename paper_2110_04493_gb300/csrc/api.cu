@@ -316,8 +316,10 @@ int64_t grid_schedule(const CsrOwned& H, cudaStream_t s, DevBuf<int32_t>& sched)
 
 // Algorithm 4.2 step 2: exact symmetry, and normality (H = H^T or H = -H^T exactly, else
 // ||H H^T - H^T H||_F <= 64 u ||H||_F^2), unless overridden.
+// normal_scale: the bound 64 u ||H||_F^2 is multiplied by it (1/sqrt(2) for the real embedding of
+// a complex matrix, whose commutator and squared norm are sqrt(2) and 2 times the complex ones).
 void classify_matrix(const CsrOwned& H, int normal_override, cudaStream_t s, HostScalars& hs, bool& symmetric,
-                     int& normal) {
+                     int& normal, double normal_scale = 1.0) {
   CsrOwned Ht;
   transpose(H.view(), s, Ht, hs);
   symmetric = csr_equal(H.view(), Ht.view(), 1.0, s, hs);
@@ -333,7 +335,7 @@ void classify_matrix(const CsrOwned& H, int normal_override, cudaStream_t s, Hos
     add(P.view(), Q.view(), -1.0, s, C, hs);
     const double nc = std::sqrt(sum_squares(C.view(), s, hs));
     const double nh2 = sum_squares(H.view(), s, hs);
-    normal = nc <= 64.0 * std::ldexp(1.0, -53) * nh2 ? 1 : 0;
+    normal = nc <= 64.0 * std::ldexp(1.0, -53) * nh2 * normal_scale ? 1 : 0;
   }
 }
 
@@ -424,6 +426,8 @@ struct sexpm_plan {
   // row schedule of the sparse products (empty: natural order)
   DevBuf<int32_t> sched;
   int64_t grid_stride = 0;
+  // complex plans: H holds the n top rows of the real embedding [X | -Y] (2n columns)
+  bool cplx = false;
   // batched plans: the captured squaring step and its arena (made on the first compute)
   GraphSquaring* graph = nullptr;
   int32_t layout_ks = -1, layout_wide = -1;  // accumulation layout chosen by sexpm_tune_batched
@@ -434,7 +438,9 @@ struct sexpm_plan {
 
 struct sexpm_result {
   cudaStream_t s = nullptr;
-  CsrOwned E;
+  CsrOwned E;                  // complex results: the pattern (E.v empty) and
+  bool cplx = false;
+  DevBuf<double> vz;           // the values, (re, im) pairs
   sexpm_stats_t st;
   std::vector<sexpm_step_stats> steps;
 };
@@ -834,6 +840,196 @@ void compute_impl(sexpm_plan_t* p, double tau, sexpm_result* res, Record* record
   st.launches = launches() - launches0;
 }
 
+// Algorithm 4.1 on the top rows of a complex iterate (decisions by |z|), then A~ = A - b_n.
+FilterOut filter_complex(const CsrD& A, int64_t n, double eps_g, double e_r, int max_iters, cudaStream_t s,
+                         CsrOwned& out, HostScalars& hs) {
+  FilterOut r;
+  Timer tf(s);
+  DevBuf<int32_t> keep(A.n ? A.n : 1, s);
+  DevBuf<double> part(A.n ? A.n : 1, s);
+  double m = 1.0;
+  double b = std::numeric_limits<double>::infinity();  // the first pass always runs
+  double eps_f = eps_g;
+  int it = 0;
+  while (b > eps_g * (1.0 + e_r)) {
+    if (it >= max_iters) fail(SEXPM_ENOCONV, "Algorithm 4.1 did not converge within " + std::to_string(max_iters) + " passes");
+    eps_f = eps_g / m;
+    b = std::sqrt(pass_complex(A, n, eps_f, keep.p, part.p, s, hs));
+    m = b / eps_f;
+    ++it;
+  }
+  compact_complex(A, n, eps_f, keep.p, s, out, hs);
+  r.t = eps_f;
+  r.b = b;
+  r.iters = it;
+  r.ms = tf.ms();
+  r.bytes = it * 12.0 * A.nnz + 12.0 * A.nnz + 12.0 * out.nnz;
+  return r;
+}
+
+// Algorithm 4.2 for a complex plan, on the top rows of the real embedding: every product forms
+// the n top rows of R(A) R(B) (B rebuilt whole by the block mirror), Algorithm 4.1 decides by
+// the modulus, and the result is read back as complex entries.  The symmetric mode and the
+// row chunking of the real path are not used.
+void compute_complex(sexpm_plan_t* p, double tau, sexpm_result* res) {
+  if (!std::isfinite(tau)) fail(SEXPM_EINVAL, "tau must be finite");
+  int dev = 0;
+  SX_CUDA(cudaGetDevice(&dev));
+  if (dev != p->device) fail(SEXPM_EINVAL, "current device differs from the plan's device");
+  cudaStream_t s = p->s;
+  HostScalars& hs = p->hs;
+  const sexpm_options& o = p->opt;
+  const int64_t n = p->H.n;
+  res->s = s;
+  res->cplx = true;
+  std::memset(&res->st, 0, sizeof(res->st));
+  sexpm_stats_t& st = res->st;
+  st.n = n;
+  Pool::reset_peak();
+  const int64_t live0 = Pool::live();
+  const int64_t launches0 = launches();
+  Timer t_all(s);
+  // step 1: tau H; ||tau H||_F^2 = sum of |z|^2 = sum of v^2 over the top rows
+  CsrD Hs = p->H.view();
+  DevBuf<double> hv(p->H.nnz, s);
+  scale_values(p->H.v.p, tau, p->H.nnz, hv.p, s);
+  Hs.v = hv.p;
+  const double normH = std::sqrt(sum_squares(Hs, s, hs));
+  st.norm_H = normH;
+  int32_t M = 0, N = 0;
+  const int rc = sexpm_choose_MN(normH, p->eps, o.n_extra, o.max_taylor, &M, &N);
+  if (rc != SEXPM_OK) fail(rc, rc == SEXPM_ENOPARAM ? "no feasible (M, N) for this tolerance" : "invalid (M, N) input");
+  st.M = M;
+  st.N = N;
+  const bool normal = (p->normal != 0) || normH == 0.0;
+  st.normal = normal ? 1 : 0;
+  st.symmetric = 0;
+  CsrOwned T;  // top rows of the running T^
+  if (M == 0) {
+    T.n = n;
+    T.rp.reset(n + 1, s);
+    SX_CUDA(cudaMemsetAsync(T.rp.p, 0, (n + 1) * sizeof(int64_t), s));
+  } else {
+    const double a = normal ? 1.0 / (1.0 + N) : 1.0 / normH;
+    st.a = a;
+    // step 3: Taylor phase on H_0 = tau H 2^-N
+    Timer t_tay(s);
+    DevBuf<double> h0v(p->H.nnz, s);
+    scale_values(hv.p, std::ldexp(1.0, -N), p->H.nnz, h0v.p, s);
+    CsrD H0 = Hs;
+    H0.v = h0v.p;
+    CsrOwned H0full;
+    block_mirror(H0, n, s, H0full);
+    const double x0 = std::ldexp(normH, -N);
+    const double r0 = sexpm_rho(M, x0);
+    const double eps_g0 = a * r0 / ((double)M * std::exp(2.0 * x0));
+    st.r0 = r0;
+    st.eps_g0 = eps_g0;
+    copy_csr(H0, s, T);
+    CsrOwned S;
+    CsrD Sv = H0;
+    CsrD none;
+    for (int i = 2; i <= M; ++i) {
+      Timer ts(s);
+      CsrOwned St;
+      SpgemmTimes tm;
+      int64_t done = 0;
+      const int64_t prod = spgemm(Sv, H0full.view(), none, (double)i, 0.0, s, St, nullptr, hs, &tm, false, &done);
+      CsrOwned Sn;
+      FilterOut fo = filter_complex(St.view(), n, eps_g0, o.e_r, o.max_filter_iters, s, Sn, hs);
+      sexpm_step_stats rec;
+      std::memset(&rec, 0, sizeof(rec));
+      rec.phase = 0;
+      rec.i = i;
+      rec.iters = fo.iters;
+      rec.eps_g = eps_g0;
+      rec.t = fo.t;
+      rec.b = fo.b;
+      rec.nnz_raw = St.nnz;
+      rec.nnz = Sn.nnz;
+      rec.products = prod;
+      rec.products_done = done;
+      rec.ms_symbolic = tm.ms_symbolic;
+      rec.ms_numeric = tm.ms_numeric;
+      rec.ms_filter = fo.ms;
+      rec.flops = 2.0 * (double)done + (double)St.nnz;
+      rec.bytes_filter = fo.bytes;
+      if (Sn.nnz == 0) {
+        rec.ms = ts.ms();
+        res->steps.push_back(rec);
+        break;
+      }
+      CsrOwned Tn;
+      add(T.view(), Sn.view(), 1.0, s, Tn, hs);
+      T = std::move(Tn);
+      S = std::move(Sn);
+      Sv = S.view();
+      rec.ms = ts.ms();
+      res->steps.push_back(rec);
+    }
+    st.ms_taylor = t_tay.ms();
+    // step 4: N filtered squarings T~ = 2 T + T T on the top rows
+    Timer t_sq(s);
+    RowStats rs;
+    for (int i = 1; i <= N; ++i) {
+      Timer ts(s);
+      CsrOwned Tfull, Tt;
+      block_mirror(T.view(), n, s, Tfull);
+      SpgemmTimes tm;
+      int64_t done = 0;
+      const int64_t prod = spgemm(T.view(), Tfull.view(), T.view(), 1.0, 2.0, s, Tt, &rs, hs, &tm, false, &done);
+      Tfull.rp.free(); Tfull.ci.free(); Tfull.v.free();
+      double normF = 1.0;
+      if (o.square_scale) {
+        // ||I + T~||_F^2 = sum |z|^2 + n + 2 sum Re z_ii over the top rows
+        const double sq = reduce_sum(rs.sq.p, n, s, hs), tr = reduce_sum(rs.diag.p, n, s, hs);
+        const double f2 = sq + (double)n + 2.0 * tr;
+        normF = std::sqrt(f2 > 0.0 ? f2 : 0.0);
+      }
+      const double eps_g = a * std::ldexp(r0, i) * normF;
+      const int64_t nnz_in = T.nnz;
+      T.rp.free(); T.ci.free(); T.v.free();
+      CsrOwned Tn;
+      FilterOut fo = filter_complex(Tt.view(), n, eps_g, o.e_r, o.max_filter_iters, s, Tn, hs);
+      sexpm_step_stats rec;
+      std::memset(&rec, 0, sizeof(rec));
+      rec.phase = 1;
+      rec.i = i;
+      rec.iters = fo.iters;
+      rec.eps_g = eps_g;
+      rec.t = fo.t;
+      rec.b = fo.b;
+      rec.norm_F = normF;
+      rec.nnz_raw = Tt.nnz;
+      rec.nnz = Tn.nnz;
+      rec.products = prod;
+      rec.products_done = done;
+      rec.ms_symbolic = tm.ms_symbolic;
+      rec.ms_numeric = tm.ms_numeric;
+      rec.ms_filter = fo.ms;
+      rec.flops = 2.0 * (double)done + 2.0 * (double)nnz_in;
+      rec.bytes_filter = fo.bytes;
+      rec.chunks = 1;
+      T = std::move(Tn);
+      rec.ms = ts.ms();
+      res->steps.push_back(rec);
+    }
+    st.ms_squaring = t_sq.ms();
+  }
+  // step 5: e^{tau H} = I + T^_N, read back as complex entries
+  Timer t_fin(s);
+  CsrOwned E;
+  add_identity(T.view(), s, E, hs);
+  T.rp.free(); T.ci.free(); T.v.free();
+  extract_complex(E.view(), n, s, res->E, res->vz, hs);
+  st.ms_final = t_fin.ms();
+  st.nnz_out = res->E.nnz;
+  st.n_steps = (int32_t)res->steps.size();
+  st.ms_total = t_all.ms();
+  st.peak_bytes = Pool::peak() - live0;
+  st.launches = launches() - launches0;
+}
+
 // A device CSR with the pattern of P and the values v (non-owning).
 CsrD with_values(const CsrD& P, const double* v) {
   CsrD d = P;
@@ -1042,7 +1238,8 @@ int sexpm_compute(sexpm_plan_t* p, double tau, sexpm_result_t** out) {
   sexpm_result* res = new sexpm_result();
   arm_alloc_failure();
   try {
-    compute_impl(p, tau, res, nullptr, p->opt.symmetric != 0);
+    if (p->cplx) compute_complex(p, tau, res);
+    else compute_impl(p, tau, res, nullptr, p->opt.symmetric != 0);
   } catch (...) {
     delete res;
     throw;
@@ -1064,6 +1261,7 @@ int sexpm_result_info(const sexpm_result_t* r, int64_t* n, int64_t* nnz) {
 int sexpm_result_copy(const sexpm_result_t* r, int64_t* row_ptr, int32_t* col, double* val, int32_t on_device) {
   SX_API_BEGIN
   if (!r) fail(SEXPM_EINVAL, "null result");
+  if (r->cplx) fail(SEXPM_EINVAL, "complex result: use sexpm_result_copy_z");
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (row_ptr) SX_CUDA(cudaMemcpyAsync(row_ptr, r->E.rp.p, (r->E.n + 1) * sizeof(int64_t), k, r->s));
   if (r->E.nnz) {
@@ -1071,6 +1269,93 @@ int sexpm_result_copy(const sexpm_result_t* r, int64_t* row_ptr, int32_t* col, d
     if (val) SX_CUDA(cudaMemcpyAsync(val, r->E.v.p, r->E.nnz * sizeof(double), k, r->s));
   }
   SX_CUDA(cudaStreamSynchronize(r->s));
+  SX_API_END
+}
+
+int sexpm_result_copy_z(const sexpm_result_t* r, int64_t* row_ptr, int32_t* col, double* val, int32_t on_device) {
+  SX_API_BEGIN
+  if (!r) fail(SEXPM_EINVAL, "null result");
+  if (!r->cplx) fail(SEXPM_EINVAL, "real result: use sexpm_result_copy");
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (row_ptr) SX_CUDA(cudaMemcpyAsync(row_ptr, r->E.rp.p, (r->E.n + 1) * sizeof(int64_t), k, r->s));
+  if (r->E.nnz) {
+    if (col) SX_CUDA(cudaMemcpyAsync(col, r->E.ci.p, r->E.nnz * sizeof(int32_t), k, r->s));
+    if (val) SX_CUDA(cudaMemcpyAsync(val, r->vz.p, 2 * r->E.nnz * sizeof(double), k, r->s));
+  }
+  SX_CUDA(cudaStreamSynchronize(r->s));
+  SX_API_END
+}
+
+int sexpm_result_is_complex(const sexpm_result_t* r, int32_t* is_complex) {
+  if (!r || !is_complex) {
+    set_last_error("null argument");
+    return SEXPM_EINVAL;
+  }
+  *is_complex = r->cplx ? 1 : 0;
+  return SEXPM_OK;
+}
+
+int sexpm_plan_z(const sexpm_csr_view* H, int64_t n, double eps, const sexpm_options* opt, void* stream,
+                 sexpm_plan_t** out) {
+  SX_API_BEGIN
+  if (!H || !out) fail(SEXPM_EINVAL, "null argument");
+  *out = nullptr;
+  if (H->n != n) fail(SEXPM_EINVAL, "n does not match the matrix");
+  if (!(eps > 0.0) || !std::isfinite(eps)) fail(SEXPM_EINVAL, "eps must be positive and finite");
+  if (H->n < 0 || H->nnz < 0 || H->n > INT32_MAX / 2) fail(SEXPM_EINVAL, "bad dimensions (n <= 2^30 for complex H)");
+  if (H->n > 0 && (!H->row_ptr || (H->nnz > 0 && (!H->col || !H->val)))) fail(SEXPM_EINVAL, "null CSR array");
+  sexpm_plan_t* p = new sexpm_plan_t();
+  try {
+    if (opt) p->opt = *opt; else sexpm_options_default(&p->opt);
+    check_options(p->opt);
+    if (p->opt.scaling != 0) fail(SEXPM_EINVAL, "complex plans use the scaling of Eq. (4.20) (scaling = 0)");
+    SX_CUDA(cudaGetDevice(&p->device));
+    p->s = static_cast<cudaStream_t>(stream);
+    p->eps = eps;
+    p->cplx = true;
+    cudaStream_t s = p->s;
+    const int64_t nn = H->n, nz = H->nnz;
+    if (!H->on_device && nn > 0) {
+      if (H->row_ptr[0] != 0 || H->row_ptr[nn] != nz) fail(SEXPM_EINVAL, "row_ptr must start at 0 and end at nnz");
+      for (int64_t i = 0; i < nn; ++i) {
+        const int64_t p0 = H->row_ptr[i], p1 = H->row_ptr[i + 1];
+        if (p1 < p0 || p1 > nz) fail(SEXPM_EINVAL, "row_ptr not monotone at row " + std::to_string(i));
+        int32_t prev = -1;
+        for (int64_t q = p0; q < p1; ++q) {
+          const int32_t c = H->col[q];
+          if (c <= prev || c >= nn) fail(SEXPM_EINVAL, "columns unsorted, duplicated or out of range in row " + std::to_string(i));
+          if (!std::isfinite(H->val[2 * q]) || !std::isfinite(H->val[2 * q + 1]))
+            fail(SEXPM_EINVAL, "non-finite value in row " + std::to_string(i));
+          prev = c;
+        }
+      }
+    }
+    DevBuf<int64_t> rp(nn + 1, s);
+    DevBuf<int32_t> ci(nz, s);
+    DevBuf<double> vz(2 * nz, s);
+    const cudaMemcpyKind k = H->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (nn > 0) SX_CUDA(cudaMemcpyAsync(rp.p, H->row_ptr, (nn + 1) * sizeof(int64_t), k, s));
+    else SX_CUDA(cudaMemsetAsync(rp.p, 0, sizeof(int64_t), s));
+    if (nz) {
+      SX_CUDA(cudaMemcpyAsync(ci.p, H->col, nz * sizeof(int32_t), k, s));
+      SX_CUDA(cudaMemcpyAsync(vz.p, H->val, 2 * nz * sizeof(double), k, s));
+    }
+    if (H->on_device && nn > 0 && !valid_complex(nn, nz, rp.p, ci.p, vz.p, s, p->hs))
+      fail(SEXPM_EINVAL, "invalid device CSR (row_ptr, column order/range or non-finite value)");
+    embed_top(nn, nz, rp.p, ci.p, vz.p, s, p->H);
+    // Hermitian H <=> its embedding is symmetric; skew-Hermitian <=> skew-symmetric; otherwise
+    // the commutator test with the complex norms
+    CsrOwned full;
+    block_mirror(p->H.view(), nn, s, full);
+    bool herm = false;
+    classify_matrix(full, p->opt.normal_override, s, p->hs, herm, p->normal, 1.0 / std::sqrt(2.0));
+    p->symmetric = false;
+    SX_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    delete p;
+    throw;
+  }
+  *out = p;
   SX_API_END
 }
 
@@ -1168,6 +1453,7 @@ int sexpm_result_spmm(const sexpm_result_t* E, const double* X, int64_t r, doubl
   SX_API_BEGIN
   if (!E || (E->E.n && r > 0 && (!X || !Y))) fail(SEXPM_EINVAL, "null argument");
   if (r < 0) fail(SEXPM_EINVAL, "r must be >= 0");
+  if (E->cplx) fail(SEXPM_EINVAL, "e^H R takes a real result");
   if (X == Y && E->E.n && r) fail(SEXPM_EINVAL, "X and Y must not overlap");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   spmm(E->E.view(), X, r, Y, s);
@@ -1179,6 +1465,7 @@ int sexpm_propagate(const sexpm_result_t* E, const double* U0, int64_t r, int32_
   SX_API_BEGIN
   if (!E || (E->E.n && r > 0 && (!U0 || !U))) fail(SEXPM_EINVAL, "null argument");
   if (r < 0 || steps < 0) fail(SEXPM_EINVAL, "r and steps must be >= 0");
+  if (E->cplx) fail(SEXPM_EINVAL, "time stepping takes a real result");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t n = E->E.n;
   const size_t bytes = (size_t)n * (size_t)r * sizeof(double);
@@ -1732,6 +2019,7 @@ int sexpm_forward_keep(sexpm_plan_t* p, double tau, int32_t ckpt_stride, sexpm_r
   *tape = nullptr;
   if (expm_out) *expm_out = nullptr;
   if (p->count > 0) fail(SEXPM_EINVAL, "the adjoint takes a plain (non-batched) plan");
+  if (p->cplx) fail(SEXPM_EINVAL, "the adjoint takes a real plan");
   if (ckpt_stride < 0) fail(SEXPM_EINVAL, "ckpt_stride must be >= 0");
   sexpm_tape_t* t = new sexpm_tape_t();
   sexpm_result* fwd = new sexpm_result();

@@ -405,6 +405,28 @@ void graph_squaring_set_layout(GraphSquaring* G, int ks_bytes, int wide);
 void graph_squarings(GraphSquaring* G, const CsrD& T0, const GraphSquaringIn& in, GraphSquaringOut& out,
                      cudaStream_t s);
 
+// ---------------------------------------------------------------- complex H
+// Z = X + iY through the real embedding R(Z) = [[X, -Y], [Y, X]]; the method keeps the n top
+// rows [X_i | -Y_i] (2n columns).  Complex values are (re, im) pairs of doubles.
+// Input check: sorted unique columns in [0, n), finite values, monotone row pointers.  Syncs s.
+bool valid_complex(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* vz, cudaStream_t s,
+                   HostScalars& hs);
+// Top rows of R(Z) from a complex CSR (device arrays).
+void embed_top(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* vz, cudaStream_t s,
+               CsrOwned& top);
+// All 2n rows of R(Z) from its top rows.
+void block_mirror(const CsrD& top, int64_t n, cudaStream_t s, CsrOwned& full);
+// Algorithm 4.1 pass deciding by |z| (pairs of columns j, n + j of a top row): returns the sum of
+// squares of the dropped entries (= sum of |z|^2), per-row kept counts in keep.  Syncs s.
+double pass_complex(const CsrD& top, int64_t n, double t, int32_t* keep, double* part, cudaStream_t s,
+                    HostScalars& hs);
+// The entries with |z| > t (keep: the counts of the pass at t).
+void compact_complex(const CsrD& top, int64_t n, double t, const int32_t* keep, cudaStream_t s, CsrOwned& out,
+                     HostScalars& hs);
+// The complex matrix of top rows: pattern (rp, ci) and values vz (2 nnz doubles).
+void extract_complex(const CsrD& top, int64_t n, cudaStream_t s, CsrOwned& pattern, DevBuf<double>& vz,
+                     HostScalars& hs);
+
 // ---------------------------------------------------------------- adjoint helpers
 // out[p] = (accumulate ? out[p] : 0) + alpha sum_l A_il B_jl + beta A_ij for every stored (i, j)
 // of P (out has P.nnz entries in P's order).

@@ -99,6 +99,9 @@ def load() -> ctypes.CDLL:
                                P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_double)]
     L.sexpm_plan_batched.argtypes = [P(CsrView), ctypes.c_int32, ctypes.c_double, P(Options), vp, P(vp)]
     L.sexpm_compute_batched.argtypes = [vp, P(ctypes.c_double), P(vp)]
+    L.sexpm_plan_z.argtypes = [P(CsrView), ctypes.c_int64, ctypes.c_double, P(Options), vp, P(vp)]
+    L.sexpm_result_is_complex.argtypes = [vp, P(ctypes.c_int32)]
+    L.sexpm_result_copy_z.argtypes = [vp, vp, vp, vp, ctypes.c_int32]
     L.sexpm_batched_graph_info.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_int32),
                                            P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_int64)]
     L.sexpm_tune_batched.argtypes = [vp, P(ctypes.c_double), ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
@@ -367,6 +370,89 @@ def expm(H, tau: float = 1.0, eps: float = 1e-12, device="cuda", **opts):
         rp, ci, v = out
         n = rp.numel() - 1
         out = torch.sparse_csr_tensor(rp, ci.to(torch.int64), v, size=(n, n))
+    return out, st
+
+
+def _make_view_z(H, keep: List[Any]) -> CsrView:
+    """A complex CSR view: val holds complex128 entries ((re, im) pairs of doubles)."""
+    rp, ci, v, n = _arrays(H)
+    try:
+        import torch
+        is_t = isinstance(rp, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        is_t = False
+    if is_t:
+        on_dev = rp.is_cuda
+        rp = rp.to(dtype=torch.int64).contiguous()
+        ci = ci.to(dtype=torch.int32).contiguous()
+        v = v.to(dtype=torch.complex128).contiguous()
+        if not (rp.is_cuda == ci.is_cuda == v.is_cuda):
+            raise ValueError("row_ptr, col and val must live on the same device")
+        keep += [rp, ci, v]
+        ptrs = (rp.data_ptr(), ci.data_ptr() if ci.numel() else None, v.data_ptr() if v.numel() else None)
+        nnz = int(ci.numel())
+    else:
+        rp = np.ascontiguousarray(rp, dtype=np.int64)
+        ci = np.ascontiguousarray(ci, dtype=np.int32)
+        v = np.ascontiguousarray(v, dtype=np.complex128)
+        keep += [rp, ci, v]
+        on_dev = False
+        ptrs = (rp.ctypes.data, ci.ctypes.data if ci.size else None, v.ctypes.data if v.size else None)
+        nnz = int(ci.size)
+    return CsrView(n, nnz, ptrs[0], ptrs[1], ptrs[2], 1 if on_dev else 0)
+
+
+class ComplexPlan(Plan):
+    """sexpm_plan_z: complex H ((row_ptr, col, val complex128[, n]) as torch tensors or numpy
+    arrays); compute() gives results whose to_torch() returns complex128 values."""
+
+    def __init__(self, H, eps: float, stream=None, **opts):  # noqa: D107 (Plan.__init__ not reused)
+        keep: List[Any] = []
+        view = _make_view_z(H, keep)
+        self._stream = _stream_ptr(stream)
+        h = ctypes.c_void_p()
+        o = options(**opts)
+        _check(load().sexpm_plan_z(ctypes.byref(view), view.n, float(eps), ctypes.byref(o), self._stream,
+                                   ctypes.byref(h)))
+        self._h = h
+        self.n = view.n
+
+    def compute(self, tau: float = 1.0) -> "ComplexResult":
+        r = ctypes.c_void_p()
+        _check(load().sexpm_compute(self._h, float(tau), ctypes.byref(r)))
+        return ComplexResult(r.value)
+
+
+class ComplexResult(Result):
+    """A library-owned complex result (sexpm_result_copy_z)."""
+
+    def to_torch(self, device="cuda"):
+        import torch
+        n, nnz = self.info()
+        rp = torch.empty(n + 1, dtype=torch.int64, device=device)
+        ci = torch.empty(nnz, dtype=torch.int32, device=device)
+        v = torch.empty(nnz, dtype=torch.complex128, device=device)
+        on_dev = 1 if rp.is_cuda else 0
+        if on_dev:
+            torch.cuda.current_stream().synchronize()
+        _check(load().sexpm_result_copy_z(self._h, rp.data_ptr(), ci.data_ptr() if nnz else None,
+                                          v.data_ptr() if nnz else None, on_dev))
+        return rp, ci, v
+
+
+def expm_complex(H, tau: float = 1.0, eps: float = 1e-12, device="cuda", **opts):
+    """e^{tau H} for complex H as (row_ptr, col, val complex128) torch tensors on `device`, plus
+    the stats dict."""
+    plan = ComplexPlan(H, eps, **opts)
+    try:
+        res = plan.compute(tau)
+        try:
+            out = res.to_torch(device)
+            st = res.stats()
+        finally:
+            res.free()
+    finally:
+        plan.close()
     return out, st
 
 
