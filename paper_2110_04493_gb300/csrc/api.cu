@@ -1904,8 +1904,8 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
   // step 5: e^{tau_b H_b} = I + T^_{N_b}, then one result per instance
   Timer t_fin(s);
   CsrOwned E;
-  T.rp.free(); T.ci.free(); T.v.free();
   if (graph_result) {
+    T.rp.free(); T.ci.free(); T.v.free();  // the Taylor phase's T^_0; the result is in the arena
     try {
       add_identity(gout.T, s, E, hs);
     } catch (const Error& e) {
@@ -1918,6 +1918,7 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
     }
   } else {
     add_identity(T.view(), s, E, hs);
+    T.rp.free(); T.ci.free(); T.v.free();
   }
   gather_row_ptr(E.rp.p, seg, count, bnd.data(), s);
   std::vector<sexpm_result*> res(count, nullptr);
