@@ -1837,7 +1837,7 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
         copy_csr(gout.T, s, Tg);
         T = std::move(Tg);
       }
-      graph_squaring_release(p->graph);
+      graph_squaring_release(p->graph, false);
       graph_squaring_note_host_steps(p->graph, Nmax - gout.steps_done);
     }
   }
@@ -1905,17 +1905,17 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
   Timer t_fin(s);
   CsrOwned E;
   if (graph_result) {
-    T.rp.free(); T.ci.free(); T.v.free();  // the Taylor phase's T^_0; the result is in the arena
-    try {
-      add_identity(gout.T, s, E, hs);
-    } catch (const Error& e) {
-      if (e.code != SEXPM_ENOMEM) throw;
-      // the arena's work buffers make room for the result, T^_N stays (it is the input)
-      CsrOwned Tg;
-      copy_csr(gout.T, s, Tg);
-      graph_squaring_release(p->graph);
-      add_identity(Tg.view(), s, E, hs);
-    }
+    T.rp.free(); T.ci.free(); T.v.free();  // the Taylor phase's T^_0
+    // T^_N is in the arena.  An arena above a quarter of the device's memory makes room for the
+    // result: its other buffers go first, then T^ (the next compute allocates the sizes of this
+    // one at once and captures the step again); a smaller one stays, with its graph, for the
+    // next compute.
+    size_t fr = 0, tot = 0;
+    SX_CUDA(cudaMemGetInfo(&fr, &tot));
+    const bool big = gout.arena_bytes > (int64_t)(tot / 4);
+    if (big) graph_squaring_release(p->graph, true);
+    add_identity(gout.T, s, E, hs);
+    if (big) graph_squaring_release(p->graph, false);
   } else {
     add_identity(T.view(), s, E, hs);
     T.rp.free(); T.ci.free(); T.v.free();

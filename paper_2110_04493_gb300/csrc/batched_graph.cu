@@ -225,7 +225,8 @@ struct GraphSquaring {
   const int64_t* seg = nullptr;
   int ks_bytes = -1;  // accumulation layout of the numeric pass (-1: the library default)
   int wide = -1;
-  int64_t capT = 0, capR = 0, capW = 0;
+  int64_t capT = 0, capR = 0, capW = 0;        // capacities allocated now
+  int64_t hintT = 0, hintR = 0, hintW = 0;     // capacities of the last run, for the next one
   // streams, events, graph
   cudaStream_t gs = nullptr, gs2 = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -254,10 +255,18 @@ struct GraphSquaring {
     exec = nullptr;
     graph = nullptr;
   }
-  void release_matrices() {
+  // Frees T~ and the word pattern (and T^ unless keep_T); their sizes stay as hints.
+  void release_matrices(bool keep_T) {
     drop_graph();
-    ciT.free(); vT.free(); ciR.free(); vR.free(); wi.free(); wb.free();
-    capT = capR = capW = 0;
+    if (capR) hintR = capR;
+    if (capW) hintW = capW;
+    ciR.free(); vR.free(); wi.free(); wb.free();
+    capR = capW = 0;
+    if (!keep_T) {
+      if (capT) hintT = capT;
+      ciT.free(); vT.free();
+      capT = 0;
+    }
   }
   ~GraphSquaring() {
     if (gs) cudaStreamSynchronize(gs);
@@ -276,10 +285,10 @@ struct GraphSquaring {
 
 GraphSquaring* graph_squaring_new() { return new GraphSquaring(); }
 void graph_squaring_free(GraphSquaring* G) { delete G; }
-void graph_squaring_release(GraphSquaring* G) {
+void graph_squaring_release(GraphSquaring* G, bool keep_T) {
   if (G) {
     if (G->gs) SX_CUDA(cudaStreamSynchronize(G->gs));
-    G->release_matrices();
+    G->release_matrices(keep_T);
   }
 }
 void graph_squaring_info(const GraphSquaring* G, int64_t* arena_bytes, int32_t* captures, int32_t* reruns,
@@ -519,7 +528,7 @@ void graph_squarings(GraphSquaring* Gp, const CsrD& T0, const GraphSquaringIn& i
   // entries, words 1/4 of T^'s), else small (a few times T^_0) and grown by the run; never above
   // the instances' dense size
   const int64_t dense = std::max<int64_t>(in.dense, 1);
-  int64_t capT = G.capT, capR = G.capR, capW = G.capW;
+  int64_t capT = G.capT ? G.capT : G.hintT, capR = G.capR ? G.capR : G.hintR, capW = G.capW ? G.capW : G.hintW;
   if (capT == 0 || capR == 0 || capW == 0) {
     if (in.arena_bytes > 0) {
       capT = std::max<int64_t>(in.arena_bytes / (12 * 4 + 2), 1);
@@ -610,18 +619,21 @@ void graph_squarings(GraphSquaring* Gp, const CsrD& T0, const GraphSquaringIn& i
     if (hst.status & kStMirror) fail(SEXPM_ECUDA, "symmetric product: an entry without its mirror partner");
     if (hst.status & kStBound) fail(SEXPM_ECUDA, "a product row exceeded the scratch bound of its size class");
     if (hst.fail_g < g_from || hst.fail_g > Nmax) fail(SEXPM_ECUDA, "captured squaring step: bad failure record");
-    // grow to the size the failing step asked for (+1/16), with room for the steps after it
+    // grow to the size the failing step asked for (+1/16; the small word pattern +1/2), with
+    // room for the steps after it
     const int64_t needR = (int64_t)hst.need_raw, needT = (int64_t)hst.need_out, needW = (int64_t)hst.need_w;
     const int64_t nR = (hst.status & kStProduct) ? std::min(dense, needR + needR / 16) : capR;
-    const int64_t nW = (hst.status & kStWords) ? std::min(dense, needW + needW / 16) : capW;
+    const int64_t nW = (hst.status & kStWords) ? std::min(dense, needW + needW / 2) : capW;
     int64_t nT = (hst.status & kStFiltered) ? std::min(dense, needT + needT / 16) : capT;
     const int f = hst.fail_g;
     keep_T = f == 1 ? T0.nnz : (int64_t)rec[f - 2].nnz;
     if ((hst.status & kStProduct) && f >= 2 && rec[f - 2].nnz_raw > 0) {
-      // a larger T~ is filtered to about the share the step before kept: room for that, so the
-      // filtered size seldom stops a step whose product has just been formed
+      // a larger T~ keeps a share of its entries that grows from step to step (the instances
+      // densify): T^ gets room for half-way between the last step's share and all of T~, so a
+      // step whose product has just been formed is seldom stopped by its filtered size
       const double share = (double)rec[f - 2].nnz / (double)rec[f - 2].nnz_raw;
-      nT = std::max(nT, std::min(dense, (int64_t)(1.1 * share * (double)nR)));
+      const double room = std::min(1.0, 1.05 * (share + 0.5 * (1.0 - share)));
+      nT = std::max(nT, std::min(dense, (int64_t)(room * (double)nR)));
     }
     if (((hst.status & kStProduct) && nR < needR) || ((hst.status & kStFiltered) && nT < needT) ||
         ((hst.status & kStWords) && nW < needW) || attempt >= 6 * Nmax + 8)

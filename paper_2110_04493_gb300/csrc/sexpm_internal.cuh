@@ -391,8 +391,9 @@ struct GraphSquaringOut {
 };
 GraphSquaring* graph_squaring_new();
 void graph_squaring_free(GraphSquaring* G);
-// Releases the arena (the graph is captured again on the next run).
-void graph_squaring_release(GraphSquaring* G);
+// Frees the arena's T~ and word pattern, and T^ unless keep_T (the graph is captured again on
+// the next run, which allocates the sizes of this one at once).
+void graph_squaring_release(GraphSquaring* G, bool keep_T);
 // Arena bytes, graph captures, resumed steps after an arena overflow, squaring steps left to the
 // host-driven launches (device memory ran out), kernels per step outside the Algorithm 4.1 loop
 // and kernels per pass of that loop.
