@@ -109,7 +109,9 @@ typedef struct {
                                by a conditional WHILE node, a fixed-capacity device arena held by the
                                plan, grown when a product does not fit (the run resumes at that step);
                                if device memory runs out the remaining steps run as host-driven
-                               launches; 0: host-driven launches.  Both give bit-identical results. */
+                               launches; an arena above a quarter of the device memory is freed at
+                               the end of each compute (the next one allocates its sizes at once);
+                               0: host-driven launches.  Both give bit-identical results. */
   int64_t batch_arena_bytes; /* first arena size for batched_graph = 1 (0, default: a few times T^_0,
                                grown by the run; never more than the instances' dense size) */
 } sexpm_options;
