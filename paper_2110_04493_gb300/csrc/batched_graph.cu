@@ -235,6 +235,7 @@ struct GraphSquaring {
   cudaGraphExec_t exec = nullptr;
   int64_t k_outer = 0, k_body = 0;  // kernels per step outside / inside the Algorithm 4.1 loop
   int captures = 0, reruns = 0, host_steps = 0;
+  bool parked = false;  // T^'s entries are in T~'s buffers (while T^ is reallocated)
   // arena
   DevBuf<int64_t> rpT, rpR, rpF, wrp, flops, scan_ts;
   DevBuf<int32_t> ciT, ciR, wi, base, words, cnt, cnt_up, lists, keep;
@@ -358,7 +359,7 @@ void setup_rows(GraphSquaring& G, const GraphSquaringIn& in, cudaStream_t s) {
 // The arena of the matrices: T^ (capT entries; the filtered result is compacted into it), T~
 // (capR entries), the word pattern of T^ (capW words) and the global-class scratch.  When T^
 // grows its first keep_T entries are kept (a resumed run continues from them).  The buffers
-// are replaced in the order T~, words, T^, so that an allocation that fails leaves T^ intact.
+// are replaced in the order T~, words, T^; T^ is parked in T~'s buffers while it is replaced.
 void setup_arena(GraphSquaring& G, int64_t capT, int64_t capR, int64_t capW, int64_t keep_T, cudaStream_t s) {
   const int ks = G.ks_bytes >= 0 ? G.ks_bytes : default_ks_bytes();
   const bool wide = G.wide >= 0 ? G.wide != 0 : default_wide_blocks();
@@ -385,14 +386,28 @@ void setup_arena(GraphSquaring& G, int64_t capT, int64_t capR, int64_t capW, int
     G.capW = capW;
   }
   if (capT != G.capT || !G.ciT.p) {
-    DevBuf<int32_t> ci(capT, s);
-    DevBuf<double> v(capT, s);
-    if (keep_T > 0) {
-      SX_CUDA(cudaMemcpyAsync(ci.p, G.ciT.p, keep_T * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-      SX_CUDA(cudaMemcpyAsync(v.p, G.vT.p, keep_T * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (keep_T > 0 && G.ciT.p && G.capR >= keep_T) {
+      // T~'s buffers hold nothing a resumed run needs: T^ waits there while it is reallocated,
+      // so the old and the new T^ are never held together
+      SX_CUDA(cudaMemcpyAsync(G.ciR.p, G.ciT.p, keep_T * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      SX_CUDA(cudaMemcpyAsync(G.vR.p, G.vT.p, keep_T * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      G.ciT.free(); G.vT.free();
+      G.capT = 0;
+      G.parked = true;
+      G.ciT.reset(capT, s); G.vT.reset(capT, s);
+      SX_CUDA(cudaMemcpyAsync(G.ciT.p, G.ciR.p, keep_T * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      SX_CUDA(cudaMemcpyAsync(G.vT.p, G.vR.p, keep_T * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      G.parked = false;
+    } else {
+      DevBuf<int32_t> ci(capT, s);
+      DevBuf<double> v(capT, s);
+      if (keep_T > 0) {
+        SX_CUDA(cudaMemcpyAsync(ci.p, G.ciT.p, keep_T * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        SX_CUDA(cudaMemcpyAsync(v.p, G.vT.p, keep_T * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
+      G.ciT = std::move(ci);
+      G.vT = std::move(v);
     }
-    G.ciT = std::move(ci);
-    G.vT = std::move(v);
     G.capT = capT;
   }
 }
@@ -560,8 +575,8 @@ void graph_squarings(GraphSquaring* Gp, const CsrD& T0, const GraphSquaringIn& i
         out.T.n = G.n;
         out.T.nnz = keep_T;
         out.T.rp = G.rpT.p;
-        out.T.ci = G.ciT.p;
-        out.T.v = G.vT.p;
+        out.T.ci = G.parked ? G.ciR.p : G.ciT.p;  // (T^ may be parked in T~'s buffers)
+        out.T.v = G.parked ? G.vR.p : G.vT.p;
       }
       break;
     }
