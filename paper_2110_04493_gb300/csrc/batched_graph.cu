@@ -263,6 +263,7 @@ struct GraphSquaring {
     if (capW) hintW = capW;
     ciR.free(); vR.free(); wi.free(); wb.free();
     capR = capW = 0;
+    parked = false;
     if (!keep_T) {
       if (capT) hintT = capT;
       ciT.free(); vT.free();
