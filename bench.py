@@ -252,6 +252,38 @@ def measure_batched(sexpm, torch, steps: int = 2):
             "squaring_fp64_gflops": gflops, "squaring_fp64_frac": gflops / peak, "steps": steps}
 
 
+def measure_complex(sexpm, torch, m: int = 600):
+    """Complex H: the Schroedinger propagator e^{i tau L} of the 2-D Dirichlet Laplacian on an m x m
+    grid (tau / h^2 = 2.253 as in the bench workload, eps = 1e-12) against the real e^{tau L} on
+    the same grid; inputs resident on the device."""
+    import numpy as np
+    from workloads import dirichlet_laplacian
+    L = dirichlet_laplacian(m, 2)
+    tau = 2.253 / (m + 1) ** 2
+    rp = torch.from_numpy(L.row_ptr).cuda()
+    ci = torch.from_numpy(L.col).cuda()
+    vr = torch.from_numpy(L.val).cuda()
+    vz = torch.from_numpy((1j * L.val).astype(np.complex128)).cuda()
+    out = {"workload": f"e^(i tau L), 2-D Dirichlet Laplacian {m}x{m} (n={L.n}), tau/h^2 = 2.253, eps 1e-12"}
+    for key, plan in (("complex", sexpm.ComplexPlan((rp, ci, vz, L.n), 1e-12)), ("real", sexpm.Plan((rp, ci, vr, L.n), 1e-12))):
+        plan.compute(tau).free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = plan.compute(tau)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = r.stats()
+        r.free()
+        plan.close()
+        formed = sum(x["products_done"] for x in st["steps"])
+        num_ms = sum(x["ms_numeric"] for x in st["steps"])
+        out[key] = {"ms": 1000.0 * dt, "M": st["M"], "N": st["N"], "nnz_out": st["nnz_out"],
+                    "real_products_formed": int(formed), "numeric_ms": num_ms,
+                    "numeric_gflops": 2.0 * formed / (num_ms * 1e6) if num_ms > 0 else 0.0}
+    out["complex_over_real"] = out["complex"]["ms"] / out["real"]["ms"]
+    return out
+
+
 def measure_adjoint(sexpm, torch, fd_edges: int = 0):
     """Adjoint form on the random-geometric-graph workload: H = beta A (n = 1e5, mean degree 10,
     weights U[0.5, 1.5], beta = 0.5, eps = 1e-12), L = sum_ij W_ij [e^H]_ij with 1e5 seeded
@@ -516,6 +548,7 @@ def run_ours(args):
                      "adjoint_rgg": measure_adjoint(sexpm, torch, args.fd_edges)}
         if args.forms:
             forms = forms or {}
+            forms["complex"] = measure_complex(sexpm, torch)
             forms["batched"] = measure_batched(sexpm, torch)
 
     cpu = None
