@@ -30,6 +30,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# DRAM bytes (read + write) of the numeric pass per formed product, from one ncu capture of every
+# k_numeric launch of the 2-D Laplacian family on a 300^2 grid (same row widths as the 1500^2
+# workload; 26.07 GB for 5.372e10 formed products); the full-size traffic is this times the
+# products formed (the full-size run holds too much device memory for a multi-pass capture).
+NUMERIC_DRAM_BYTES_PER_PRODUCT = 26.071323392e9 / 53716599900
 METRIC = "time-to-e^{tau H} (reported as e^{tau H} computations per second, whole job)"
 
 
@@ -572,7 +577,10 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "alu", "kernel": "k_numeric (sparse product numeric pass, FP64)",
                          "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                         "frac": achieved / FP64_PEAK_GFLOPS,
+                         "traffic": NUMERIC_DRAM_BYTES_PER_PRODUCT * sum(r["products_done"] for r in st["steps"]),
+                         "traffic_note": "bytes per e^{tau H} (all k_numeric launches): ncu DRAM bytes per formed "
+                                         "product on the 300^2 case times the products formed here",
                          "peak_kind": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)"},
             "roofline_hbm": {"bound": "hbm", "kernel": "Algorithm 4.1 passes + scan + compaction",
                              "achieved": f_gbs, "peak": hbm_peak, "unit": "GB/s",
