@@ -867,9 +867,9 @@ FilterOut filter_complex(const CsrD& A, int64_t n, double eps_g, double e_r, int
   return r;
 }
 
-// Algorithm 4.2 for a complex plan, on the top rows of the real embedding: every product forms
-// the n top rows of R(A) R(B) (B rebuilt whole by the block mirror), Algorithm 4.1 decides by
-// the modulus, and the result is read back as complex entries.  The symmetric mode and the
+// Algorithm 4.2 for a complex plan, on the even rows of the real embedding: every product forms
+// the n even rows of R(A) R(B) (B rebuilt whole by the mirror), Algorithm 4.1 decides by the
+// modulus, and the result is read back as complex entries.  The symmetric mode and the
 // row chunking of the real path are not used.
 void compute_complex(sexpm_plan_t* p, double tau, sexpm_result* res) {
   if (!std::isfinite(tau)) fail(SEXPM_EINVAL, "tau must be finite");
@@ -981,8 +981,8 @@ void compute_complex(sexpm_plan_t* p, double tau, sexpm_result* res) {
       Tfull.rp.free(); Tfull.ci.free(); Tfull.v.free();
       double normF = 1.0;
       if (o.square_scale) {
-        // ||I + T~||_F^2 = sum |z|^2 + n + 2 sum Re z_ii over the top rows
-        const double sq = reduce_sum(rs.sq.p, n, s, hs), tr = reduce_sum(rs.diag.p, n, s, hs);
+        // ||I + T~||_F^2 = sum |z|^2 + n + 2 sum Re z_ii over the even rows (Re z_ii at column 2i)
+        const double sq = reduce_sum(rs.sq.p, n, s, hs), tr = trace_re(Tt.view(), s, hs);
         const double f2 = sq + (double)n + 2.0 * tr;
         normF = std::sqrt(f2 > 0.0 ? f2 : 0.0);
       }
@@ -1018,8 +1018,9 @@ void compute_complex(sexpm_plan_t* p, double tau, sexpm_result* res) {
   }
   // step 5: e^{tau H} = I + T^_N, read back as complex entries
   Timer t_fin(s);
-  CsrOwned E;
-  add_identity(T.view(), s, E, hs);
+  CsrOwned E, I2;
+  identity_pairs(n, s, I2);
+  add(T.view(), I2.view(), 1.0, s, E, hs);
   T.rp.free(); T.ci.free(); T.v.free();
   extract_complex(E.view(), n, s, res->E, res->vz, hs);
   st.ms_final = t_fin.ms();

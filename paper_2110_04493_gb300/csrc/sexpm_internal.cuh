@@ -407,23 +407,28 @@ void graph_squarings(GraphSquaring* G, const CsrD& T0, const GraphSquaringIn& in
                      cudaStream_t s);
 
 // ---------------------------------------------------------------- complex H
-// Z = X + iY through the real embedding R(Z) = [[X, -Y], [Y, X]]; the method keeps the n top
-// rows [X_i | -Y_i] (2n columns).  Complex values are (re, im) pairs of doubles.
+// Z = X + iY through the real embedding R(Z) = X (x) I_2 + Y (x) J; the method keeps its n even
+// rows (row i: the pairs (2j: Re z_ij, 2j + 1: -Im z_ij), 2n columns).  Complex values are
+// (re, im) pairs of doubles.  ("top rows" below are these even rows.)
 // Input check: sorted unique columns in [0, n), finite values, monotone row pointers.  Syncs s.
 bool valid_complex(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* vz, cudaStream_t s,
                    HostScalars& hs);
 // Top rows of R(Z) from a complex CSR (device arrays).
 void embed_top(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* vz, cudaStream_t s,
                CsrOwned& top);
-// All 2n rows of R(Z) from its top rows.
+// All 2n rows of R(Z) from its even rows (rows 2i and 2i + 1).
 void block_mirror(const CsrD& top, int64_t n, cudaStream_t s, CsrOwned& full);
-// Algorithm 4.1 pass deciding by |z| (pairs of columns j, n + j of a top row): returns the sum of
+// Algorithm 4.1 pass deciding by |z| (pairs of columns 2j, 2j + 1 of a row): returns the sum of
 // squares of the dropped entries (= sum of |z|^2), per-row kept counts in keep.  Syncs s.
 double pass_complex(const CsrD& top, int64_t n, double t, int32_t* keep, double* part, cudaStream_t s,
                     HostScalars& hs);
 // The entries with |z| > t (keep: the counts of the pass at t).
 void compact_complex(const CsrD& top, int64_t n, double t, const int32_t* keep, cudaStream_t s, CsrOwned& out,
                      HostScalars& hs);
+// The identity in the even-row layout (row i: (2i: 1, 2i + 1: 0)).
+void identity_pairs(int64_t n, cudaStream_t s, CsrOwned& I);
+// sum_i Re z_ii of the even rows (the value at column 2i of row i).  Syncs s.
+double trace_re(const CsrD& top, cudaStream_t s, HostScalars& hs);
 // The complex matrix of top rows: pattern (rp, ci) and values vz (2 nnz doubles).
 void extract_complex(const CsrD& top, int64_t n, cudaStream_t s, CsrOwned& pattern, DevBuf<double>& vz,
                      HostScalars& hs);
