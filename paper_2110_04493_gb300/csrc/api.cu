@@ -1747,7 +1747,49 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
   for (int b = 0; b < count; ++b) done_b[b] = M[b] <= 1;
   std::vector<int64_t> bnd(count + 1);
   const double inf = std::numeric_limits<double>::infinity();
-  for (int i = 2; i <= Mmax; ++i) {
+  // the captured steps' description of the batch (Taylor terms and squarings)
+  GraphSquaringIn gi;
+  gi.count = count;
+  gi.n = n;
+  gi.inst = inst;
+  gi.seg = seg;
+  gi.N = N;
+  gi.M = M;
+  gi.a = a;
+  gi.r0 = r0;
+  gi.eps_g0 = eps_g0;
+  gi.nb.resize(count);
+  for (int b = 0; b < count; ++b) {
+    const int64_t nb = p->row0[b + 1] - p->row0[b];
+    gi.nb[b] = (double)nb;
+    gi.n_max = std::max(gi.n_max, nb);
+    gi.dense += nb * nb;
+  }
+  gi.arena_bytes = o.batch_arena_bytes;
+  gi.sym = sym;
+  gi.square_scale = o.square_scale != 0;
+  gi.e_r = o.e_r;
+  gi.max_iters = o.max_filter_iters;
+  // the Taylor terms as captured graphs (one per term); host-driven launches when they are off
+  // or the arena does not fit in device memory
+  bool taylor_done = false;
+  if (o.batched_graph != 0 && Mmax >= 2 && Mmax <= 128) {
+    if (!p->graph) p->graph = graph_squaring_new();
+    graph_squaring_set_layout(p->graph, p->layout_ks, p->layout_wide);
+    GraphSquaringOut tout;
+    try {
+      graph_taylor(p->graph, H0, gi, tout, s);
+      CsrOwned Tg;
+      copy_csr(tout.T, s, Tg);
+      T = std::move(Tg);
+      for (const auto& st : tout.steps) steps.push_back(st);
+      taylor_done = true;
+    } catch (const Error& e) {
+      if (e.code != SEXPM_ENOMEM) throw;
+      graph_squaring_release(p->graph, false);
+    }
+  }
+  for (int i = 2; i <= Mmax && !taylor_done; ++i) {
     Timer ts(s);
     CsrOwned St;
     SpgemmTimes tm;
@@ -1809,26 +1851,6 @@ int sexpm_compute_batched(sexpm_plan_t* p, const double* taus, sexpm_result_t** 
   if (use_graph) {
     if (!p->graph) p->graph = graph_squaring_new();
     graph_squaring_set_layout(p->graph, p->layout_ks, p->layout_wide);
-    GraphSquaringIn gi;
-    gi.count = count;
-    gi.n = n;
-    gi.inst = inst;
-    gi.seg = seg;
-    gi.N = N;
-    gi.a = a;
-    gi.r0 = r0;
-    gi.nb.resize(count);
-    for (int b = 0; b < count; ++b) {
-      const int64_t nb = p->row0[b + 1] - p->row0[b];
-      gi.nb[b] = (double)nb;
-      gi.n_max = std::max(gi.n_max, nb);
-      gi.dense += nb * nb;
-    }
-    gi.arena_bytes = o.batch_arena_bytes;
-    gi.sym = sym;
-    gi.square_scale = o.square_scale != 0;
-    gi.e_r = o.e_r;
-    gi.max_iters = o.max_filter_iters;
     graph_squarings(p->graph, T.view(), gi, gout, s);
     for (const auto& st : gout.steps) steps.push_back(st);
     g_start = gout.steps_done + 1;

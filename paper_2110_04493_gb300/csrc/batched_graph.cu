@@ -48,6 +48,7 @@ struct GState {
   unsigned long long need_raw;  // largest unfiltered product requested (entries)
   unsigned long long need_out;  // largest filtered product requested (entries)
   unsigned long long need_w;    // largest word pattern requested (words)
+  unsigned long long need_sum;  // largest T^_0 + S^_i requested (entries)
 };
 
 // One record per squaring step, written on the device.
@@ -209,6 +210,57 @@ __global__ void k_g_record(GState* st, GStepRec* rec, int count, const unsigned 
   }
 }
 
+// Taylor term i: an instance whose series has ended (an empty S^ term) or whose degree M_b is
+// below i forms nothing this step.
+__global__ void k_t_begin(GState* st, int i, int count, const int32_t* M, const uint8_t* done, uint8_t* frozen) {
+  if (threadIdx.x == 0) {
+    st->g = i;
+    st->loop = 0;
+  }
+  for (int b = threadIdx.x; b < count; b += blockDim.x) frozen[b] = (done[b] || i > M[b]) ? 1 : 0;
+}
+
+// Taylor bound of every instance (eps_g^(0), Eq. 4.14); an instance that forms nothing drops
+// everything (t = +inf) and is not iterated.
+__global__ void k_t_alg41_init(int count, const uint8_t* frozen, const double* eps0, double* eps, double* t,
+                               double* m, double* bval, int32_t* iters, int32_t* conv) {
+  for (int b = threadIdx.x; b < count; b += blockDim.x) {
+    iters[b] = 0;
+    bval[b] = 0.0;
+    if (frozen[b]) {
+      conv[b] = 1;
+      t[b] = __longlong_as_double(0x7ff0000000000000ll);
+      eps[b] = 0.0;
+    } else {
+      eps[b] = eps0[b];
+      m[b] = 1.0;
+      t[b] = eps0[b];
+      conv[b] = 0;
+    }
+  }
+}
+
+// After the term: an instance whose S^_i has no entry ends its series.
+__global__ void k_t_done(const GState* st, int count, const int64_t* seg, const int64_t* rpS, uint8_t* done) {
+  if (st->status) return;
+  for (int b = threadIdx.x; b < count; b += blockDim.x)
+    if (rpS[seg[b + 1]] == rpS[seg[b]]) done[b] = 1;
+}
+
+// T^_0 <- the sum T^_0 + S^_i (row pointers and entries), when the step succeeded.
+__global__ void k_t_copy(const GState* st, int64_t n, const int64_t* rpN, const int32_t* ciN, const double* vN,
+                         int64_t* rpT, int32_t* ciT, double* vT) {
+  if (st->status) return;
+  const int64_t nnz = rpN[n];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i <= n; i += stride) rpT[i] = rpN[i];
+  for (int64_t q = t0; q < nnz; q += stride) {
+    ciT[q] = ciN[q];
+    vT[q] = vN[q];
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
@@ -235,6 +287,19 @@ struct GraphSquaring {
   cudaGraphExec_t exec = nullptr;
   int64_t k_outer = 0, k_body = 0;  // kernels per step outside / inside the Algorithm 4.1 loop
   int captures = 0, reruns = 0, host_steps = 0;
+  // Taylor phase: H_0, S^ (capS; the filtered term is compacted into it), T^_0 and the sum
+  // T^_0 + S^_i (capT0 each); one graph per term (index i)
+  int64_t capS = 0, capT0 = 0, capH = 0;
+  DevBuf<int64_t> rpH, rpS, rpSN, rpT0, rpTN;
+  DevBuf<int32_t> ciH, ciS, ciSN, ciT0, ciTN, Mb;
+  DevBuf<double> vH, vS, vSN, vT0, vTN, eps0;
+  int t_captures = 0, t_reruns = 0;
+  int64_t t_outer = 0, t_body = 0;  // kernels per Taylor term outside / inside its Algorithm 4.1 loop
+  DevBuf<uint8_t> done;
+  DevBuf<GStepRec> recT;
+  std::vector<cudaGraph_t> tgraph;
+  std::vector<cudaGraphExec_t> texec;
+  int t_captured_for = 0;  // the M_max the Taylor graphs were captured for (0: none)
   bool parked = false;  // T^'s entries are in T~'s buffers (while T^ is reallocated)
   // arena
   DevBuf<int64_t> rpT, rpR, rpF, wrp, flops, scan_ts;
@@ -255,6 +320,13 @@ struct GraphSquaring {
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr;
     graph = nullptr;
+    for (auto& e : texec)
+      if (e) cudaGraphExecDestroy(e);
+    for (auto& g : tgraph)
+      if (g) cudaGraphDestroy(g);
+    texec.clear();
+    tgraph.clear();
+    t_captured_for = 0;
   }
   // Frees T~ and the word pattern (and T^ unless keep_T); their sizes stay as hints.
   void release_matrices(bool keep_T) {
@@ -269,6 +341,8 @@ struct GraphSquaring {
       ciT.free(); vT.free();
       capT = 0;
     }
+    ciS.free(); vS.free(); ciSN.free(); vSN.free(); ciT0.free(); vT0.free(); ciTN.free(); vTN.free();
+    capS = capT0 = 0;
   }
   ~GraphSquaring() {
     if (gs) cudaStreamSynchronize(gs);
@@ -699,6 +773,316 @@ void graph_squarings(GraphSquaring* Gp, const CsrD& T0, const GraphSquaringIn& i
   count_launches(kernels);
   out.launches = kernels;
   out.arena_bytes = G.arena_bytes();
+}
+
+
+// ---------------------------------------------------------------- the Taylor phase
+
+namespace {
+
+// Buffers of the Taylor phase: H_0 (capH), S^ and the new term (capS each), T^_0 and the sum
+// (capT0 each); T~ and the word pattern are the squarings' (capR, capW).  S^ and T^_0 keep their
+// first keepS / keepT0 entries when they grow.
+void setup_taylor(GraphSquaring& G, int64_t capH, int64_t capS, int64_t capT0, int64_t capR, int64_t capW,
+                  int64_t keepS, int64_t keepT0, cudaStream_t s) {
+  const int64_t n = G.n;
+  if (G.rpS.count != (size_t)(n + 1)) {
+    G.drop_graph();
+    G.rpH.reset(n + 1, s); G.rpS.reset(n + 1, s); G.rpSN.reset(n + 1, s);
+    G.rpT0.reset(n + 1, s); G.rpTN.reset(n + 1, s);
+  }
+  if (G.Mb.count != (size_t)G.count) {
+    G.drop_graph();
+    G.Mb.reset(G.count, s); G.eps0.reset(G.count, s); G.done.reset(G.count, s);
+  }
+  if (!G.recT.p) G.recT.reset(kRecCap, s);
+  if (capR != G.capR || !G.ciR.p) {
+    G.drop_graph();
+    G.ciR.free(); G.vR.free();
+    G.capR = 0;
+    G.ciR.reset(capR, s); G.vR.reset(capR, s);
+    G.capR = capR;
+  }
+  if (capW != G.capW || !G.wi.p) {
+    G.drop_graph();
+    G.wi.free(); G.wb.free();
+    G.capW = 0;
+    G.wi.reset(capW, s); G.wb.reset(capW, s);
+    G.capW = capW;
+  }
+  if (capH != G.capH || !G.ciH.p) {
+    G.drop_graph();
+    G.ciH.reset(capH, s); G.vH.reset(capH, s);
+    G.capH = capH;
+  }
+  auto grow = [&](DevBuf<int32_t>& ci, DevBuf<double>& v, int64_t cap, int64_t keep) {
+    DevBuf<int32_t> c2(cap, s);
+    DevBuf<double> v2(cap, s);
+    if (keep > 0) {
+      SX_CUDA(cudaMemcpyAsync(c2.p, ci.p, keep * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      SX_CUDA(cudaMemcpyAsync(v2.p, v.p, keep * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    ci = std::move(c2);
+    v = std::move(v2);
+  };
+  if (capS != G.capS || !G.ciS.p) {
+    G.drop_graph();
+    grow(G.ciS, G.vS, capS, G.ciS.p ? keepS : 0);
+    G.ciSN.reset(capS, s); G.vSN.reset(capS, s);
+    G.capS = capS;
+  }
+  if (capT0 != G.capT0 || !G.ciT0.p) {
+    G.drop_graph();
+    grow(G.ciT0, G.vT0, capT0, G.ciT0.p ? keepT0 : 0);
+    G.ciTN.reset(capT0, s); G.vTN.reset(capT0, s);
+    G.capT0 = capT0;
+  }
+}
+
+// Captures Taylor term i into G.tgraph[i] / G.texec[i].
+void capture_taylor(GraphSquaring& G, int i) {
+  DevProduct P = product_bufs(G);
+  dev_product_prepare(P);
+  const int64_t n = G.n;
+  const int c = G.count;
+  CsrD S, H, R, SN, T0;
+  S.n = H.n = R.n = SN.n = T0.n = n;
+  S.rp = G.rpS.p; S.ci = G.ciS.p; S.v = G.vS.p;
+  H.rp = G.rpH.p; H.ci = G.ciH.p; H.v = G.vH.p;
+  R.rp = G.rpR.p; R.ci = G.ciR.p; R.v = G.vR.p;
+  SN.rp = G.rpSN.p; SN.ci = G.ciSN.p; SN.v = G.vSN.p;
+  T0.rp = G.rpT0.p; T0.ci = G.ciT0.p; T0.v = G.vT0.p;
+  GState* st = G.st.p;
+  int32_t* status = &st->status;
+  cudaStream_t gs = G.gs, gs2 = G.gs2;
+  int dev_sms = 0;
+  SX_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, G.device));
+  const int64_t L0 = launches();
+  bool body_open = false;
+  cudaGraph_t graph = nullptr;
+  SX_CUDA(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+  try {
+    k_t_begin<<<1, 256, 0, gs>>>(st, i, c, G.Mb.p, G.done.p, G.frozen_inst.p);
+    SX_CUDA(cudaGetLastError());
+    row_flags(G.inst, G.frozen_inst.p, n, G.frozen_row.p, gs);
+    // S~_i = S^_{i-1} H_0 / i
+    dev_product(S, H, false, (double)i, 0.0, false, G.frozen_row.p, P, gs);
+    k_t_alg41_init<<<1, 256, 0, gs>>>(c, G.frozen_inst.p, G.eps0.p, G.eps.p, G.t.p, G.m.p, G.bval.p, G.iters.p,
+                                     G.conv.p);
+    SX_CUDA(cudaGetLastError());
+    count_launches(2);
+    const int64_t L1 = launches();
+    // Algorithm 4.1 per instance (WHILE node)
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    SX_CUDA(cudaStreamGetCaptureInfo(gs, &cs, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle h;
+    SX_CUDA(cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t cn;
+    SX_CUDA(cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &np));
+    SX_CUDA(cudaStreamUpdateCaptureDependencies(gs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    SX_CUDA(cudaStreamBeginCaptureToGraph(gs2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    body_open = true;
+    filter_pass_seg_dev(R, G.inst, G.t.p, G.keep.p, G.part.p, status, gs2);
+    seg_sums_dev(G.part.p, G.seg, c, G.bsum.p, gs2);
+    k_g_alg41_update<<<1, 256, 0, gs2>>>(st, c, G.e_r, G.max_iters, G.eps.p, G.t.p, G.m.p, G.bsum.p, G.bval.p,
+                                        G.iters.p, G.conv.p, h);
+    SX_CUDA(cudaGetLastError());
+    count_launches(1);
+    cudaGraph_t body = nullptr;
+    body_open = false;
+    SX_CUDA(cudaStreamEndCapture(gs2, &body));
+    const int64_t L2 = launches();
+    // S^_i (new term) and T^_0 + S^_i, each within its capacity; then, when the step succeeded,
+    // the instances whose series ended, S^ <- S^_i and T^_0 <- the sum
+    scan_counts_dev(G.keep.p, n, G.rpSN.p, G.scan_ts.p, gs);
+    k_g_cap_check_out<<<1, 1, 0, gs>>>(st, G.rpSN.p + n, G.capS);
+    compact_seg_dev(R, G.inst, G.t.p, G.rpSN.p, G.ciSN.p, G.vSN.p, status, gs);
+    add_dev(T0, SN, 1.0, G.cnt.p, G.rpTN.p, G.scan_ts.p, G.ciTN.p, G.vTN.p, G.capT0, status, &st->need_sum, kStSum,
+            gs);
+    k_t_done<<<1, 256, 0, gs>>>(st, c, G.seg, G.rpSN.p, G.done.p);
+    k_t_copy<<<(unsigned)(dev_sms * 4), 256, 0, gs>>>(st, n, G.rpSN.p, G.ciSN.p, G.vSN.p, G.rpS.p, G.ciS.p, G.vS.p);
+    k_t_copy<<<(unsigned)(dev_sms * 4), 256, 0, gs>>>(st, n, G.rpTN.p, G.ciTN.p, G.vTN.p, G.rpT0.p, G.ciT0.p,
+                                                     G.vT0.p);
+    k_g_record<<<1, 256, 0, gs>>>(st, G.recT.p, c, G.ctr.p, dev_product_products_index(), dev_product_formed_index(),
+                                  G.rpR.p + n, G.rpSN.p + n, G.frozen_inst.p, G.eps.p, G.t.p, G.bval.p, G.iters.p);
+    SX_CUDA(cudaGetLastError());
+    count_launches(6);
+    const int64_t L3 = launches();
+    G.t_outer = (L1 - L0) + (L3 - L2);
+    G.t_body = L2 - L1;
+    SX_CUDA(cudaStreamEndCapture(gs, &graph));
+  } catch (...) {
+    cudaGraph_t tmp = nullptr;
+    if (body_open && cudaStreamEndCapture(gs2, &tmp) == cudaSuccess && tmp) cudaGraphDestroy(tmp);
+    tmp = nullptr;
+    if (cudaStreamEndCapture(gs, &tmp) == cudaSuccess && tmp) cudaGraphDestroy(tmp);
+    cudaGetLastError();
+    throw;
+  }
+  count_launches(-(launches() - L0));  // captured, not launched
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    SX_CUDA(e);
+  }
+  G.tgraph[i] = graph;
+  G.texec[i] = ex;
+  ++G.t_captures;
+}
+
+}  // namespace
+
+void graph_taylor(GraphSquaring* Gp, const CsrD& H0, const GraphSquaringIn& in, GraphSquaringOut& out,
+                  cudaStream_t s) {
+  GraphSquaring& G = *Gp;
+  const int count = in.count;
+  int Mmax = 0;
+  for (int b = 0; b < count; ++b) Mmax = std::max(Mmax, in.M[b]);
+  if (Mmax > kRecCap) fail(SEXPM_EINVAL, "the captured Taylor terms keep at most 128 records");
+  int dev = 0;
+  SX_CUDA(cudaGetDevice(&dev));
+  if (G.device >= 0 && dev != G.device) fail(SEXPM_EINVAL, "current device differs from the captured graph's device");
+  setup_rows(G, in, s);
+  out.steps.clear();
+  out.reruns = 0;
+  out.steps_done = 0;
+  const int64_t n = G.n;
+  const int64_t dense = std::max<int64_t>(in.dense, 1);
+  // capacities: those held, else a few times H_0 (grown by the run)
+  int64_t capS = G.capS ? G.capS : std::min(dense, std::max<int64_t>(8 * H0.nnz, 1 << 20));
+  int64_t capT0 = G.capT0 ? G.capT0 : capS;
+  int64_t capR = G.capR ? G.capR : (G.hintR ? G.hintR : std::min(dense, 4 * capS));
+  int64_t capW = G.capW ? G.capW : (G.hintW ? G.hintW : std::max<int64_t>(capS / 4, 1));
+  capW = std::max(capW, H0.nnz);  // the word pattern of H_0 (at most one word per entry)
+  capR = std::min(capR, dense);
+  std::vector<GStepRec> rec(Mmax + 1);
+  std::vector<double> ms_step(Mmax + 1, 0.0);
+  int g_from = 2;
+  int64_t keepS = 0, keepT0 = 0;
+  GState hst;
+  for (int attempt = 0;; ++attempt) {
+    setup_taylor(G, H0.nnz, capS, capT0, capR, capW, keepS, keepT0, s);
+    if (G.t_captured_for != Mmax || (int)G.texec.size() < Mmax + 1) {
+      for (auto& e : G.texec)
+        if (e) cudaGraphExecDestroy(e);
+      for (auto& g : G.tgraph)
+        if (g) cudaGraphDestroy(g);
+      G.texec.assign(Mmax + 1, nullptr);
+      G.tgraph.assign(Mmax + 1, nullptr);
+      for (int i = 2; i <= Mmax; ++i) capture_taylor(G, i);
+      G.t_captured_for = Mmax;
+    }
+    if ((int)G.ev_step.size() < Mmax + 1) {
+      for (int k = (int)G.ev_step.size(); k <= Mmax; ++k) {
+        cudaEvent_t e;
+        SX_CUDA(cudaEventCreate(&e));
+        G.ev_step.push_back(e);
+      }
+    }
+    SX_CUDA(cudaEventRecord(G.ev_in, s));
+    SX_CUDA(cudaStreamWaitEvent(G.gs, G.ev_in, 0));
+    if (attempt == 0) {
+      // inputs: H_0, S^_1 = H_0, T^_0 = H_0; an instance of degree M_b <= 1 has no further term
+      std::vector<uint8_t> done0(count);
+      for (int b = 0; b < count; ++b) done0[b] = in.M[b] <= 1 ? 1 : 0;
+      for (int64_t* rp : {G.rpH.p, G.rpS.p, G.rpT0.p})
+        SX_CUDA(cudaMemcpyAsync(rp, H0.rp, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, G.gs));
+      if (H0.nnz) {
+        for (int32_t* ci : {G.ciH.p, G.ciS.p, G.ciT0.p})
+          SX_CUDA(cudaMemcpyAsync(ci, H0.ci, H0.nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, G.gs));
+        for (double* v : {G.vH.p, G.vS.p, G.vT0.p})
+          SX_CUDA(cudaMemcpyAsync(v, H0.v, H0.nnz * sizeof(double), cudaMemcpyDeviceToDevice, G.gs));
+      }
+      SX_CUDA(cudaMemcpyAsync(G.Mb.p, in.M.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, G.gs));
+      SX_CUDA(cudaMemcpyAsync(G.eps0.p, in.eps_g0.data(), count * sizeof(double), cudaMemcpyHostToDevice, G.gs));
+      SX_CUDA(cudaMemcpyAsync(G.done.p, done0.data(), count, cudaMemcpyHostToDevice, G.gs));
+    }
+    std::memset(&hst, 0, sizeof(hst));
+    SX_CUDA(cudaMemcpyAsync(G.st.p, &hst, sizeof(GState), cudaMemcpyHostToDevice, G.gs));
+    SX_CUDA(cudaEventRecord(G.ev_step[g_from - 1], G.gs));
+    for (int i = g_from; i <= Mmax; ++i) {
+      SX_CUDA(cudaGraphLaunch(G.texec[i], G.gs));
+      SX_CUDA(cudaEventRecord(G.ev_step[i], G.gs));
+    }
+    int64_t nS = 0, nT0 = 0;
+    SX_CUDA(cudaMemcpyAsync(&hst, G.st.p, sizeof(GState), cudaMemcpyDeviceToHost, G.gs));
+    SX_CUDA(cudaMemcpyAsync(rec.data(), G.recT.p, (Mmax + 1) * sizeof(GStepRec), cudaMemcpyDeviceToHost, G.gs));
+    SX_CUDA(cudaMemcpyAsync(&nS, G.rpS.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, G.gs));
+    SX_CUDA(cudaMemcpyAsync(&nT0, G.rpT0.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, G.gs));
+    SX_CUDA(cudaStreamSynchronize(G.gs));
+    const int done_to = hst.status ? hst.fail_g - 1 : Mmax;
+    for (int i = g_from; i <= done_to; ++i) {
+      float ms = 0.f;
+      SX_CUDA(cudaEventElapsedTime(&ms, G.ev_step[i - 1], G.ev_step[i]));
+      ms_step[i] = ms;
+    }
+    if (hst.status == 0) {
+      out.T.n = n;
+      out.T.nnz = nT0;
+      out.T.rp = G.rpT0.p;
+      out.T.ci = G.ciT0.p;
+      out.T.v = G.vT0.p;
+      break;
+    }
+    if (hst.status & kStNoConv)
+      fail(SEXPM_ENOCONV, "Algorithm 4.1 did not converge within " + std::to_string(in.max_iters) + " passes");
+    if (hst.status & (kStMirror | kStBound)) fail(SEXPM_ECUDA, "captured Taylor term: internal bound exceeded");
+    if (hst.fail_g < g_from || hst.fail_g > Mmax) fail(SEXPM_ECUDA, "captured Taylor term: bad failure record");
+    const int64_t needR = (int64_t)hst.need_raw, needS = (int64_t)hst.need_out, needW = (int64_t)hst.need_w,
+                  needT = (int64_t)hst.need_sum;
+    const int64_t nR = (hst.status & kStProduct) ? std::min(dense, needR + needR / 4) : capR;
+    const int64_t nS2 = (hst.status & kStFiltered) ? std::min(dense, needS + needS / 4) : capS;
+    const int64_t nW = (hst.status & kStWords) ? std::min(dense, needW + needW / 2) : capW;
+    const int64_t nT = (hst.status & kStSum) ? std::min(dense, needT + needT / 4) : capT0;
+    if (((hst.status & kStProduct) && nR < needR) || ((hst.status & kStFiltered) && nS2 < needS) ||
+        ((hst.status & kStWords) && nW < needW) || ((hst.status & kStSum) && nT < needT) || attempt >= 6 * Mmax + 8)
+      fail(SEXPM_EOVERFLOW, "the batched Taylor terms do not fit the device arena");
+    g_from = hst.fail_g;
+    keepS = nS;
+    keepT0 = nT0;
+    capR = nR;
+    capS = std::max(nS2, nS);
+    capW = nW;
+    capT0 = std::max(nT, nT0);
+    ++G.t_reruns;
+    ++out.reruns;
+  }
+  SX_CUDA(cudaEventRecord(G.ev_out, G.gs));
+  SX_CUDA(cudaStreamWaitEvent(s, G.ev_out, 0));
+  // the terms' records, up to the first term that was empty for every instance (the series ended)
+  int64_t kernels = 0;
+  for (int i = 2; i <= Mmax; ++i) {
+    const GStepRec& r = rec[i - 1];
+    sexpm_step_stats st;
+    std::memset(&st, 0, sizeof(st));
+    st.phase = 0;
+    st.i = i;
+    st.iters = r.iters_max;
+    st.t = r.t_max;
+    st.eps_g = r.eps_max;
+    st.b = r.b_max;
+    st.nnz_raw = (int64_t)r.nnz_raw;
+    st.nnz = (int64_t)r.nnz;
+    st.products = (int64_t)r.products;
+    st.products_done = (int64_t)r.formed;
+    st.flops = 2.0 * (double)r.formed + (double)r.nnz_raw;
+    st.ms = ms_step[i];
+    out.steps.push_back(st);
+    kernels += G.t_outer + G.t_body * r.loops;
+    if (r.nnz == 0) break;
+  }
+  count_launches(kernels);
+  out.launches = kernels;
+  out.steps_done = Mmax;
 }
 
 }  // namespace sexpm

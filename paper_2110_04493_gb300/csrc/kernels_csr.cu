@@ -179,7 +179,9 @@ __global__ void k_scan_apply(const int32_t* cnt, int64_t n, const int64_t* tile_
 }
 
 // ---- C = A + beta B, thread per row merge (rows of the Taylor terms are short)
-__global__ void k_add_count(CsrD A, CsrD B, int32_t* cnt) {
+// A non-null `status` that is set (an operand was not formed) stops the add kernels.
+__global__ void k_add_count(CsrD A, CsrD B, int32_t* cnt, const int32_t* status) {
+  if (status && *status) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   int64_t p = A.rp[i], pe = A.rp[i + 1], q = B.rp[i], qe = B.rp[i + 1];
@@ -193,7 +195,9 @@ __global__ void k_add_count(CsrD A, CsrD B, int32_t* cnt) {
   cnt[i] = c + (int)(pe - p) + (int)(qe - q);
 }
 
-__global__ void k_add_write(CsrD A, CsrD B, double beta, const int64_t* rp, int32_t* ci, double* v) {
+__global__ void k_add_write(CsrD A, CsrD B, double beta, const int64_t* rp, int32_t* ci, double* v,
+                            const int32_t* status) {
+  if (status && *status) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   int64_t p = A.rp[i], pe = A.rp[i + 1], q = B.rp[i], qe = B.rp[i + 1];
@@ -560,13 +564,13 @@ void add(const CsrD& A, const CsrD& B, double beta, cudaStream_t s, CsrOwned& C,
   C.rp.reset(n + 1, s);
   DevBuf<int32_t> cnt(n ? n : 1, s);
   const unsigned g = (unsigned)((n + 255) / 256);
-  if (n) k_add_count<<<g, 256, 0, s>>>(A, B, cnt.p);
+  if (n) k_add_count<<<g, 256, 0, s>>>(A, B, cnt.p, nullptr);
   SX_CUDA(cudaGetLastError());
   count_launches(n ? 1 : 0);
   C.nnz = scan_counts(cnt.p, n, C.rp.p, s, hs);
   C.ci.reset(C.nnz, s);
   C.v.reset(C.nnz, s);
-  if (n) k_add_write<<<g, 256, 0, s>>>(A, B, beta, C.rp.p, C.ci.p, C.v.p);
+  if (n) k_add_write<<<g, 256, 0, s>>>(A, B, beta, C.rp.p, C.ci.p, C.v.p, nullptr);
   SX_CUDA(cudaGetLastError());
   count_launches(n ? 1 : 0);
 }
@@ -640,6 +644,28 @@ void filter_pass_seg(const CsrD& A, const int32_t* inst, const double* t_inst, i
     count_launches(1);
   }
   seg_sums(row_part, seg, count, sums_host, s);
+}
+
+// status |= bit when the size at *rp_n exceeds cap (need = the largest size asked for); skipped
+// once the status is set.
+__global__ void k_csr_cap_check(const int64_t* rp_n, int64_t cap, int32_t* status, unsigned long long* need,
+                                int32_t bit) {
+  if (*status) return;
+  const long long total = *rp_n;
+  atomicMax(need, (unsigned long long)total);
+  if (total > cap) atomicOr(status, bit);
+}
+
+void add_dev(const CsrD& A, const CsrD& B, double beta, int32_t* cnt, int64_t* rp_out, int64_t* ts, int32_t* ci_out,
+             double* v_out, int64_t cap, int32_t* status, unsigned long long* need, int32_t bit, cudaStream_t s) {
+  const int64_t n = A.n;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  k_add_count<<<g, 256, 0, s>>>(A, B, cnt, status);
+  scan_counts_dev(cnt, n, rp_out, ts, s);
+  k_csr_cap_check<<<1, 1, 0, s>>>(rp_out + n, cap, status, need, bit);
+  k_add_write<<<g, 256, 0, s>>>(A, B, beta, rp_out, ci_out, v_out, status);
+  SX_CUDA(cudaGetLastError());
+  count_launches(3);
 }
 
 void seg_sums_dev(const double* x, const int64_t* seg, int count, double* out, cudaStream_t s) {

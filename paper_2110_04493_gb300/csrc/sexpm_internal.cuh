@@ -303,6 +303,11 @@ void filter_pass_seg_dev(const CsrD& A, const int32_t* inst, const double* t_ins
 void compact_seg_dev(const CsrD& A, const int32_t* inst, const double* t_inst, const int64_t* rp_out, int32_t* ci_out,
                      double* v_out, const int32_t* status, cudaStream_t s);
 
+// C = A + beta B into rp_out/ci_out/v_out (capacity cap): when the sum does not fit, status
+// gets `bit` and nothing is written; nothing runs while the status is set.
+void add_dev(const CsrD& A, const CsrD& B, double beta, int32_t* cnt, int64_t* rp_out, int64_t* ts, int32_t* ci_out,
+             double* v_out, int64_t cap, int32_t* status, unsigned long long* need, int32_t bit, cudaStream_t s);
+
 // Status bits of a device-sized step.
 constexpr int32_t kStProduct = 1;   // the unfiltered product exceeded its capacity
 constexpr int32_t kStFiltered = 2;  // the filtered product exceeded its capacity
@@ -310,6 +315,7 @@ constexpr int32_t kStMirror = 4;    // symmetric mode: an entry without its mirr
 constexpr int32_t kStNoConv = 8;    // Algorithm 4.1 reached its iteration cap
 constexpr int32_t kStBound = 16;    // a row exceeded the scratch bound of its size class
 constexpr int32_t kStWords = 32;    // the word pattern of B exceeded its capacity
+constexpr int32_t kStSum = 64;      // a sum (T^_0 + S^_i) exceeded its capacity
 
 // Buffers of C = (A B)/div + beta D formed with sizes decided on the device: every buffer is
 // allocated beforehand (capacities in entries), B and D share one pattern (D is B or absent).
@@ -380,6 +386,9 @@ struct GraphSquaringIn {
   bool sym = false, square_scale = true;
   double e_r = 0.1;
   int max_iters = 100;
+  // Taylor phase (graph_taylor): degree M_b and threshold eps_g^(0) per instance
+  std::vector<int32_t> M;
+  std::vector<double> eps_g0;
 };
 struct GraphSquaringOut {
   CsrD T;                 // T^ after steps_done squarings (block diagonal), in the arena
@@ -405,6 +414,12 @@ void graph_squaring_set_layout(GraphSquaring* G, int ks_bytes, int wide);
 // Runs the squarings from T^_0 (T0, device, block diagonal).  Orders itself after s and s after it.
 void graph_squarings(GraphSquaring* G, const CsrD& T0, const GraphSquaringIn& in, GraphSquaringOut& out,
                      cudaStream_t s);
+// The Taylor phase (Algorithm 4.2 step 3 for every instance) as one captured graph per term:
+// from H_0 (device, block diagonal), T^_0 = H_0 + sum_i S^_i into out.T (in the arena, valid
+// until the next run); out.steps are the terms' records (phase 0).  Orders itself after s and s
+// after it.  Requires max M_b <= 128.
+void graph_taylor(GraphSquaring* G, const CsrD& H0, const GraphSquaringIn& in, GraphSquaringOut& out,
+                  cudaStream_t s);
 
 // ---------------------------------------------------------------- complex H
 // Z = X + iY through the real embedding R(Z) = X (x) I_2 + Y (x) J; the method keeps its n even
