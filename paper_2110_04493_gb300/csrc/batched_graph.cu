@@ -435,19 +435,24 @@ void setup_rows(GraphSquaring& G, const GraphSquaringIn& in, cudaStream_t s) {
 // (capR entries), the word pattern of T^ (capW words) and the global-class scratch.  When T^
 // grows its first keep_T entries are kept (a resumed run continues from them).  The buffers
 // are replaced in the order T~, words, T^; T^ is parked in T~'s buffers while it is replaced.
-void setup_arena(GraphSquaring& G, int64_t capT, int64_t capR, int64_t capW, int64_t keep_T, cudaStream_t s) {
+// The global-memory class's scratch of the products (for the current layout).
+void setup_scratch(GraphSquaring& G, cudaStream_t s) {
   const int ks = G.ks_bytes >= 0 ? G.ks_bytes : default_ks_bytes();
   const bool wide = G.wide >= 0 ? G.wide != 0 : default_wide_blocks();
   int64_t ss, sg, ns, ng;
   dev_product_scratch(G.n_max, ks, wide, ss, sg, ns, ng);
-  const bool scratch_same = ss == G.sym_stride && sg == G.sym_grid && ns == G.num_stride && ng == G.num_grid;
-  if (capT == G.capT && capR == G.capR && capW == G.capW && scratch_same && G.ciT.p) return;
+  const bool same = ss == G.sym_stride && sg == G.sym_grid && ns == G.num_stride && ng == G.num_grid;
+  if (same && G.gs_num.p && G.gs_sym.p) return;
   G.drop_graph();
-  if (!scratch_same || !G.gs_num.p) {
-    G.sym_stride = ss; G.sym_grid = sg; G.num_stride = ns; G.num_grid = ng;
-    G.gs_sym.reset((size_t)(ss * sg), s);
-    G.gs_num.reset((size_t)(ns * ng), s);
-  }
+  G.sym_stride = ss; G.sym_grid = sg; G.num_stride = ns; G.num_grid = ng;
+  G.gs_sym.reset((size_t)(ss * sg), s);
+  G.gs_num.reset((size_t)(ns * ng), s);
+}
+
+void setup_arena(GraphSquaring& G, int64_t capT, int64_t capR, int64_t capW, int64_t keep_T, cudaStream_t s) {
+  setup_scratch(G, s);
+  if (capT == G.capT && capR == G.capR && capW == G.capW && G.ciT.p) return;
+  G.drop_graph();
   if (capR != G.capR || !G.ciR.p) {
     G.ciR.free(); G.vR.free();
     G.capR = 0;
@@ -786,6 +791,7 @@ namespace {
 void setup_taylor(GraphSquaring& G, int64_t capH, int64_t capS, int64_t capT0, int64_t capR, int64_t capW,
                   int64_t keepS, int64_t keepT0, cudaStream_t s) {
   const int64_t n = G.n;
+  setup_scratch(G, s);
   if (G.rpS.count != (size_t)(n + 1)) {
     G.drop_graph();
     G.rpH.reset(n + 1, s); G.rpS.reset(n + 1, s); G.rpSN.reset(n + 1, s);
@@ -863,13 +869,13 @@ void capture_taylor(GraphSquaring& G, int i) {
   SX_CUDA(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
   try {
     k_t_begin<<<1, 256, 0, gs>>>(st, i, c, G.Mb.p, G.done.p, G.frozen_inst.p);
-    SX_CUDA(cudaGetLastError());
+    check_cuda(cudaGetLastError(), "taylor: after k_t_begin");
     row_flags(G.inst, G.frozen_inst.p, n, G.frozen_row.p, gs);
     // S~_i = S^_{i-1} H_0 / i
     dev_product(S, H, false, (double)i, 0.0, false, G.frozen_row.p, P, gs);
     k_t_alg41_init<<<1, 256, 0, gs>>>(c, G.frozen_inst.p, G.eps0.p, G.eps.p, G.t.p, G.m.p, G.bval.p, G.iters.p,
                                      G.conv.p);
-    SX_CUDA(cudaGetLastError());
+    check_cuda(cudaGetLastError(), "taylor: after k_t_alg41_init");
     count_launches(2);
     const int64_t L1 = launches();
     // Algorithm 4.1 per instance (WHILE node)
@@ -894,7 +900,7 @@ void capture_taylor(GraphSquaring& G, int i) {
     seg_sums_dev(G.part.p, G.seg, c, G.bsum.p, gs2);
     k_g_alg41_update<<<1, 256, 0, gs2>>>(st, c, G.e_r, G.max_iters, G.eps.p, G.t.p, G.m.p, G.bsum.p, G.bval.p,
                                         G.iters.p, G.conv.p, h);
-    SX_CUDA(cudaGetLastError());
+    check_cuda(cudaGetLastError(), "taylor: after k_g_alg41_update");
     count_launches(1);
     cudaGraph_t body = nullptr;
     body_open = false;
@@ -913,7 +919,7 @@ void capture_taylor(GraphSquaring& G, int i) {
                                                      G.vT0.p);
     k_g_record<<<1, 256, 0, gs>>>(st, G.recT.p, c, G.ctr.p, dev_product_products_index(), dev_product_formed_index(),
                                   G.rpR.p + n, G.rpSN.p + n, G.frozen_inst.p, G.eps.p, G.t.p, G.bval.p, G.iters.p);
-    SX_CUDA(cudaGetLastError());
+    check_cuda(cudaGetLastError(), "taylor: after k_g_record");
     count_launches(6);
     const int64_t L3 = launches();
     G.t_outer = (L1 - L0) + (L3 - L2);

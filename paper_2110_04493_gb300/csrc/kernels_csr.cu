@@ -664,7 +664,7 @@ void add_dev(const CsrD& A, const CsrD& B, double beta, int32_t* cnt, int64_t* r
   scan_counts_dev(cnt, n, rp_out, ts, s);
   k_csr_cap_check<<<1, 1, 0, s>>>(rp_out + n, cap, status, need, bit);
   k_add_write<<<g, 256, 0, s>>>(A, B, beta, rp_out, ci_out, v_out, status);
-  SX_CUDA(cudaGetLastError());
+  check_cuda(cudaGetLastError(), "add_dev");
   count_launches(3);
 }
 
