@@ -426,6 +426,7 @@ void setup_rows(GraphSquaring& G, const GraphSquaringIn& in, cudaStream_t s) {
   // zeroed once so that no kernel ever reads an unwritten value
   SX_CUDA(cudaMemsetAsync(G.part.p, 0, n * sizeof(double), s));
   SX_CUDA(cudaMemsetAsync(G.keep.p, 0, n * sizeof(int32_t), s));
+  SX_CUDA(cudaMemsetAsync(G.cnt.p, 0, n * sizeof(int32_t), s));
   SX_CUDA(cudaMemsetAsync(G.bsum.p, 0, c * sizeof(double), s));
   SX_CUDA(cudaMemsetAsync(G.sq.p, 0, c * sizeof(double), s));
   SX_CUDA(cudaMemsetAsync(G.tr.p, 0, c * sizeof(double), s));

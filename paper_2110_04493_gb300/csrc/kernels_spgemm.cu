@@ -1050,10 +1050,12 @@ __global__ void k_dev_cap_check(const int64_t* rp_n, int64_t cap, int32_t* statu
 // Before a pass over the row lists: a row whose need exceeds the global class's scratch stride
 // (a bound the buffers were sized by) stops the step; when the step is stopped every list is
 // emptied so the row kernels form nothing.
+// (A step already stopped -- its sizes come from skipped kernels -- is not judged.)
 __global__ void k_dev_gate(unsigned long long* counts, const unsigned long long* maxneed, long long global_cap,
                            int32_t* status) {
   if (threadIdx.x != 0) return;
-  if (counts[kClasses - 1] > 0 && maxneed[kClasses - 1] > (unsigned long long)global_cap) atomicOr(status, kStBound);
+  if (*status == 0 && counts[kClasses - 1] > 0 && maxneed[kClasses - 1] > (unsigned long long)global_cap)
+    atomicOr(status, kStBound);
   if (*status)
     for (int c = 0; c < kClasses; ++c) counts[c] = 0;
 }
