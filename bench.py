@@ -212,9 +212,11 @@ def measure_batched(sexpm, torch, steps: int = 2):
         l0 = sexpm.kernel_launches()
         t0 = time.perf_counter()
         st = None
+        mmax = 0
         for _ in range(steps):
             res = bplan.compute(taus)
             st = res[0].stats()
+            mmax = max(r.stats()["M"] for r in res)
             for r in res:
                 r.free()
         torch.cuda.synchronize()
@@ -224,10 +226,11 @@ def measure_batched(sexpm, torch, steps: int = 2):
         bplan.close()
         sexpm.release_memory()
         sq = [x for x in st["steps"] if x["phase"] == 1]
-        return dt, launches, info, sum(x["products_done"] for x in sq), st["ms_squaring"], len(sq), st["peak_bytes"]
+        return (dt, launches, info, sum(x["products_done"] for x in sq), st["ms_squaring"], len(sq), st["peak_bytes"],
+                max(mmax - 1, 0))
 
-    t_graph, l_graph, info, formed, sq_ms, nsq, peak_g = run_batched(1)
-    t_host, l_host, _, _, sq_ms_host, _, peak_h = run_batched(0)
+    t_graph, l_graph, info, formed, sq_ms, nsq, peak_g, nterms = run_batched(1)
+    t_host, l_host, _, _, sq_ms_host, _, peak_h, _ = run_batched(0)
     plans = [sexpm.Plan(d, BATCH_EPS) for d in devs]
     for p, t in zip(plans, taus):      # warm-up
         p.compute(t).free()
@@ -248,7 +251,8 @@ def measure_batched(sexpm, torch, steps: int = 2):
             "batched_host_driven_ms": 1000.0 * t_host, "per_matrix_loop_ms": 1000.0 * t_loop,
             "speedup_vs_loop": t_loop / t_graph, "launches_batched": int(l_graph),
             "launches_batched_host_driven": int(l_host), "launches_loop": int(l_loop),
-            "graph": {"squaring_steps": nsq, "graph_launches_per_batch": nsq - info["host_steps"],
+            "graph": {"squaring_steps": nsq, "taylor_terms": nterms,
+                      "graph_launches_per_batch": nterms + nsq - info["host_steps"],
                       "kernels_per_step": info["kernels_per_step"], "kernels_per_alg41_pass": info["kernels_per_pass"],
                       "arena_bytes": info["arena_bytes"], "resumed_steps": info["reruns"],
                       "host_driven_steps": info["host_steps"]},

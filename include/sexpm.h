@@ -104,8 +104,9 @@ typedef struct {
                                of (M, N) (sexpm_choose_MN_refined), in r_0 = rho(M, h_{M,N}) and in
                                eps_g^(0) = a r_0 / (M e^{2 h_{M,N}}) */
   int32_t refine_kmax;      /* highest power of tau H the refined norm uses (odd, >= 3; default 41) */
-  int32_t batched_graph;    /* batched plans: 1 (default): the squaring phase runs as one captured CUDA
-                               graph per step -- sizes decided on the device, Algorithm 4.1 iterated
+  int32_t batched_graph;    /* batched plans: 1 (default): every Taylor term and every squaring step
+                               runs as one captured CUDA graph -- sizes decided on the device,
+                               Algorithm 4.1 iterated
                                by a conditional WHILE node, a fixed-capacity device arena held by the
                                plan, grown when a product does not fit (the run resumes at that step);
                                if device memory runs out the remaining steps run as host-driven
@@ -268,7 +269,8 @@ int sexpm_choose_MN_refined(double norm_H, const double* pnorms, int32_t kmax, d
  * instances are stored as one block-diagonal matrix, so every step of Algorithm 4.2 runs as one
  * set of kernel launches for the whole batch (the sparse product's row kernels are persistent
  * over per-size-class row lists that hold the rows of every instance); with
- * sexpm_options.batched_graph = 1 each squaring step is one replay of a captured CUDA graph.  Validation, symmetry and normality are per
+ * sexpm_options.batched_graph = 1 each Taylor term and each squaring step is one replay of a
+ * captured CUDA graph.  Validation, symmetry and normality are per
  * instance.  eps is shared.  Not in the paper (a batched form of Algorithm 4.2). */
 int sexpm_plan_batched(const sexpm_csr_view* Hs, int32_t count, double eps, const sexpm_options* opt,
                        void* stream, sexpm_plan_t** out);

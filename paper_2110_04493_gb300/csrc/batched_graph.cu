@@ -1,8 +1,9 @@
-// The squaring phase of the batched method (Algorithm 4.2 step 4 for every instance of a
-// block-diagonal batch) as a CUDA graph: one squaring step -- T~_i = 2 T^_{i-1} + T^_{i-1}^2 for
-// all instances, each instance's Algorithm 4.1 with its own bound eps_g^(i) = a_b 2^i r_0,b
-// ||I + T~_i||_F, and the compaction -- is captured once and replayed N_max times with no host
-// involvement between the steps.
+// The batched method (Algorithm 4.2 steps 3 and 4 for every instance of a block-diagonal batch)
+// as CUDA graphs: one squaring step -- T~_i = 2 T^_{i-1} + T^_{i-1}^2 for all instances, each
+// instance's Algorithm 4.1 with its own bound eps_g^(i) = a_b 2^i r_0,b ||I + T~_i||_F, and the
+// compaction -- is captured once and replayed N_max times with no host involvement between the
+// steps; each Taylor term (S~_i = S^_{i-1} H_0 / i, Algorithm 4.1 with eps_g^(0), T^_0 += S^_i) is
+// one captured graph of its own (the divisor i is a kernel argument), the same machinery.
 //
 //  * Sizes are decided on the device.  Every buffer lives in a device arena allocated
 //    beforehand with fixed capacities (T^, the unfiltered T~, the word pattern of T^ and the
