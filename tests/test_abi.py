@@ -154,3 +154,38 @@ def test_host_alpha_hat_and_refined_choice_match_the_oracle(lib):
     MN = sexpm.choose_MN_refined(nL, pl, 1e-12)
     assert MN == O.choose_MN_refined(nL, pl, 1e-12)
     assert MN[1] < O.choose_MN(nL, 1e-12)[1]   # the refined norm needs fewer squarings
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a struct of include/sexpm.h, from a C program compiled with gcc."""
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"sexpm.h\"\nint main(void) {\n"
+    src += f'  printf("%zu\\n", sizeof({struct}));\n'
+    for f in fields:
+        src += f'  printf("%zu\\n", offsetof({struct}, {f}));\n'
+    src += "  return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run([gcc, "-std=c99", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("cname,pyname", [("sexpm_options", "Options"), ("sexpm_step_stats", "StepStats"),
+                                          ("sexpm_stats_t", "Stats"), ("sexpm_csr_view", "CsrView")])
+def test_binding_structs_match_the_header_layout(cname, pyname):
+    """The ctypes mirrors of the C structs have the header's size and field offsets (a field added
+    on one side only would shift every later field)."""
+    from paper_2110_04493_gb300 import sexpm
+    py = getattr(sexpm, pyname)
+    fields = [f for f, _ in py._fields_ if not f.endswith("_")]
+    size, offs = _c_layout(cname, fields)
+    assert ctypes.sizeof(py) == size
+    assert [getattr(py, f).offset for f in fields] == offs
