@@ -154,11 +154,15 @@ def test_transpose_with_long_rows_matches_scipy(sx, long_len):
     the result equals scipy's transpose entry for entry."""
     rng = np.random.default_rng(long_len)
     n = 40000
-    A = sp.random(n, n, density=4 / n, random_state=np.random.RandomState(1), format="lil")
+    B = sp.random(n, n, density=4 / n, random_state=np.random.RandomState(1), format="coo")
+    keep = (B.col != 5) & (B.col != 777)  # columns 5 and 777 are set below
     rows = rng.choice(n, size=long_len, replace=False)
-    A[rows, 5] = rng.uniform(-1, 1, long_len)[:, None]
-    A[rows[:long_len // 2], 777] = rng.uniform(-1, 1, long_len // 2)[:, None]
-    A = sp.csr_matrix(A)
+    half = rows[:long_len // 2]
+    r = np.concatenate([B.row[keep], rows, half])
+    c = np.concatenate([B.col[keep], np.full(long_len, 5), np.full(half.size, 777)])
+    v = np.concatenate([B.data[keep], rng.uniform(-1, 1, long_len), rng.uniform(-1, 1, half.size)])
+    A = sp.csr_matrix((v, (r, c)), shape=(n, n))
+    A.sum_duplicates()
     A.sort_indices()
     rp, ci, v = sx.transpose(torch_csr(CSR.from_scipy(A)))
     G = to_scipy(rp, ci, v, n)
