@@ -154,13 +154,15 @@ def test_transpose_with_long_rows_matches_scipy(sx, long_len):
     the result equals scipy's transpose entry for entry."""
     rng = np.random.default_rng(long_len)
     n = 40000
-    B = sp.random(n, n, density=4 / n, random_state=np.random.RandomState(1), format="coo")
-    keep = (B.col != 5) & (B.col != 777)  # columns 5 and 777 are set below
+    # about 4 random entries per row (positions drawn independently; repeats are summed)
+    br, bc = rng.integers(0, n, 4 * n), rng.integers(0, n, 4 * n)
+    keep = (bc != 5) & (bc != 777)  # columns 5 and 777 are set below
     rows = rng.choice(n, size=long_len, replace=False)
     half = rows[:long_len // 2]
-    r = np.concatenate([B.row[keep], rows, half])
-    c = np.concatenate([B.col[keep], np.full(long_len, 5), np.full(half.size, 777)])
-    v = np.concatenate([B.data[keep], rng.uniform(-1, 1, long_len), rng.uniform(-1, 1, half.size)])
+    r = np.concatenate([br[keep], rows, half])
+    c = np.concatenate([bc[keep], np.full(long_len, 5), np.full(half.size, 777)])
+    v = np.concatenate([rng.uniform(-1, 1, int(keep.sum())), rng.uniform(-1, 1, long_len),
+                        rng.uniform(-1, 1, half.size)])
     A = sp.csr_matrix((v, (r, c)), shape=(n, n))
     A.sum_duplicates()
     A.sort_indices()
