@@ -6,6 +6,8 @@ include/sexpm.h); :mod:`paper_2110_04493_gb300.sexpm` is its Python binding.
 """
 from .sexpm import (  # noqa: F401
     BatchedPlan,
+    ComplexPlan,
+    ComplexResult,
     Plan,
     Result,
     adjoint,
@@ -14,6 +16,7 @@ from .sexpm import (  # noqa: F401
     expm,
     expm_autograd,
     expm_batched,
+    expm_complex,
     filter_csr,
     load,
     rho,
