@@ -113,8 +113,8 @@ typedef struct {
                                launches; an arena above a quarter of the device memory is freed at
                                the end of each compute (the next one allocates its sizes at once);
                                0: host-driven launches.  Both give bit-identical results. */
-  int64_t batch_arena_bytes; /* first arena size for batched_graph = 1 (0, default: a few times T^_0,
-                               grown by the run; never more than the instances' dense size) */
+  int64_t batch_arena_bytes; /* first arena size for batched_graph = 1 (0, default: a few times H_0
+                               and T^_0, grown by the run; never more than the instances' dense size) */
 } sexpm_options;
 
 typedef struct sexpm_plan sexpm_plan_t;

@@ -965,13 +965,16 @@ void graph_taylor(GraphSquaring* Gp, const CsrD& H0, const GraphSquaringIn& in, 
   out.steps_done = 0;
   const int64_t n = G.n;
   const int64_t dense = std::max<int64_t>(in.dense, 1);
-  // capacities: those held, else a few times H_0 (grown by the run)
-  int64_t capS = G.capS ? G.capS : std::min(dense, std::max<int64_t>(8 * H0.nnz, 1 << 20));
-  int64_t capT0 = G.capT0 ? G.capT0 : capS;
-  int64_t capR = G.capR ? G.capR : (G.hintR ? G.hintR : std::min(dense, 4 * capS));
+  // capacities: those held, else from the caller's budget, else a few times H_0 (grown by the
+  // run); S^ and T^_0 start as H_0, so they hold at least its entries
+  const int64_t budget = in.arena_bytes > 0 ? std::max<int64_t>(in.arena_bytes / 64, 1) : 0;
+  int64_t capS = G.capS ? G.capS : (budget ? budget : std::min(dense, std::max<int64_t>(8 * H0.nnz, 1 << 20)));
+  capS = std::max(capS, H0.nnz);
+  int64_t capT0 = std::max(G.capT0 ? G.capT0 : capS, H0.nnz);
+  int64_t capR = G.capR ? G.capR : (G.hintR ? G.hintR : (budget ? budget : std::min(dense, 4 * capS)));
   int64_t capW = G.capW ? G.capW : (G.hintW ? G.hintW : std::max<int64_t>(capS / 4, 1));
   capW = std::max(capW, H0.nnz);  // the word pattern of H_0 (at most one word per entry)
-  capR = std::min(capR, dense);
+  capR = std::max<int64_t>(std::min(capR, dense), 1);
   std::vector<GStepRec> rec(Mmax + 1);
   std::vector<double> ms_step(Mmax + 1, 0.0);
   int g_from = 2;

@@ -139,9 +139,9 @@ def test_graph_step_equals_host_driven_launches_bit_for_bit(sx, symmetric):
 
 
 def test_graph_arena_overflow_grows_and_resumes(sx):
-    """A first arena far too small for the products: the device flags the overflow, the host
-    grows the arena to the recorded size and resumes at that step; the result is the same bit
-    for bit as the host-driven launches."""
+    """A first arena far too small for the products (Taylor terms and squarings): the device flags
+    the overflow, the host grows the arena to the recorded size and resumes at that step; the
+    result is the same bit for bit as the host-driven launches."""
     items = laplacian_batch(count=6, seed=9, side_lo=6, side_hi=16, tau_lo=1e-3, tau_hi=1e-2)
     g, info = _batch_results(sx, items, 1e-12, batched_graph=1, batch_arena_bytes=4096)
     h, _ = _batch_results(sx, items, 1e-12, batched_graph=0)
